@@ -1,0 +1,191 @@
+/*
+ * ptp.h -- C ABI of the GB300 (sm_103a) Parallel Toplesets Propagation
+ * library: approximate geodesic distance maps on triangle meshes
+ * (Romero Calla, Fuentes Perez, Montenegro, "A minimalistic approach for
+ * fast computation of geodesic distances on triangular meshes").
+ *
+ * Problem (Sec. 3.1, "Discrete distance maps"): given a triangle mesh
+ * T = (V, E, F) and a source set S subset of V, compute d_S : V -> R, the
+ * geodesic distance from every vertex to S.
+ *
+ * Pipeline, one call per stage:
+ *   ptp_mesh_create   vertices + faces -> device mesh with the
+ *                     vertex -> incident-triangle lists;
+ *   ptp_toplesets     sources -> toplesets V_r (breadth-first levels,
+ *                     Sec. 3.1 Definition) and the mesh renumbered in
+ *                     topleset order (Sec. 3.3);
+ *   ptp_distance      the PTP iteration over the sliding update band
+ *                     (Sec. 3.2, Eq. lower_band / upper_band) into a
+ *                     caller-owned device buffer in the ORIGINAL vertex order.
+ *   ptp_geodesic      all three stages in one call (host or device buffers).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns a ptp_status; PTP_OK is 0.
+ *  - Streams: `stream` is a cudaStream_t passed as an opaque pointer
+ *    (NULL = the legacy default stream).  Work is enqueued on it; a function
+ *    only blocks where its comment says so.
+ *  - Pointers: `ptr_kind` says whether array arguments are host memory
+ *    (PTP_HOST) or device memory of the current device (PTP_DEVICE).  Inputs
+ *    are copied; the caller keeps ownership of every buffer it passes.
+ *  - Handles are opaque, own their device memory (stream-ordered
+ *    allocations on the creating stream) and are released by the matching
+ *    *_destroy.  A handle may be used from one host thread at a time.
+ *  - Indices are 0-based int32; vertex positions are float32 xyz triples.
+ */
+#ifndef PTP_H
+#define PTP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ptp_status {
+    PTP_OK = 0,
+    PTP_ERR_ARG = 1,             /* null pointer, bad size or bad parameter        */
+    PTP_ERR_INDEX = 2,           /* a face or source index is out of range         */
+    PTP_ERR_DEGENERATE_FACE = 3, /* a face repeats a vertex                         */
+    PTP_ERR_CUDA = 4,            /* a CUDA runtime call failed                      */
+    PTP_ERR_NOT_CONVERGED = 5,   /* max_iter reached; the distances are written     */
+    PTP_ERR_TIMEOUT = 6,         /* a device-side wait hit its limit; kernel exited */
+    PTP_ERR_NOMEM = 7,           /* device allocation failed                        */
+    PTP_ERR_TOO_LARGE = 8        /* a size exceeds this entry point's limit         */
+} ptp_status;
+
+enum { PTP_HOST = 0, PTP_DEVICE = 1 };
+
+typedef struct ptp_mesh ptp_mesh;
+typedef struct ptp_toplesets_s ptp_toplesets_t;
+
+/* Parameters of ptp_distance.  Fill with ptp_params_default first. */
+typedef struct ptp_params {
+    double eps;        /* relative-change threshold of Eq. lower_band (Sec. 3.2);
+                          the paper uses 1e-3 in all experiments                   */
+    double eps_abs;    /* absolute slack: a vertex of V_{i_{k-1}} passes when
+                          |d_k - d_{k-1}| < eps * d_{k-1} + eps_abs or the change
+                          is exactly 0 (paper: eps_abs = 0)                        */
+    int64_t max_iter;  /* iteration cap; 0 = 8 * rho + 64                          */
+    int32_t block;     /* threads per CTA of the window kernel; 0 = auto           */
+    int32_t grid;      /* CTAs of the window kernel; 0 = all co-resident CTAs      */
+    void *trace;       /* optional DEVICE buffer of trace_cap ptp_trace_rec, one per
+                          iteration, or NULL                                       */
+    int64_t trace_cap;
+} ptp_params;
+
+/* One record per PTP iteration k (written only when params.trace is set). */
+typedef struct ptp_trace_rec {
+    int32_t i;         /* lower band bound used at iteration k, i_{k-1}            */
+    int32_t j;         /* upper band bound j_k (Eq. upper_band)                    */
+    int32_t active;    /* band vertices recomputed (some neighbour changed)        */
+    int32_t changed;   /* band vertices whose distance changed                     */
+    float maxrel;      /* max relative change over V_{i_{k-1}}                     */
+    int32_t advanced;  /* 1 if i_k = i_{k-1} + 1 (Eq. lower_band)                 */
+    double errsum;     /* FP64 sum of relative changes over V_{i_{k-1}}            */
+} ptp_trace_rec;
+
+typedef struct ptp_stats {
+    int64_t iterations;      /* K, iterations run                                   */
+    int64_t band_updates;    /* sum over k of |B_k minus S| (the paper's work count) */
+    int64_t active_updates;  /* vertex updates actually recomputed                  */
+    int64_t changed;         /* vertex updates that lowered the distance            */
+    int64_t fp64_solves;     /* triangle solves taken in FP64 (near-degenerate)     */
+    int32_t rho;             /* number of toplesets                                 */
+    int32_t status;          /* ptp_status of the device-side run                   */
+} ptp_stats;
+
+/* Human-readable name of a status code (static storage). */
+const char *ptp_status_str(ptp_status s);
+
+/* Defaults: eps = 1e-3 and eps_abs = 0 (Sec. 3.2, the paper's setting),
+ * max_iter = 0 (auto), block = grid = 0 (auto), no trace. */
+ptp_status ptp_params_default(ptp_params *p);
+
+/*
+ * Build the device mesh (Sec. 3.1, T = (V, E, F); Sec. 3.3 stores it as a
+ * compact half-edge structure, here as vertex -> incident-triangle lists).
+ *  xyz    [n_verts * 3] float32, row-major vertex positions.
+ *  faces  [n_faces * 3] int32, 0-based, either orientation.
+ *  Validates every face: PTP_ERR_INDEX (index outside [0, n_verts)),
+ *  PTP_ERR_DEGENERATE_FACE (a face repeats a vertex), PTP_ERR_ARG
+ *  (null pointer, n_verts < 3, n_faces < 1, or more than 2^31 - 1 corners).
+ *  Blocks until validation has finished on `stream`.
+ */
+ptp_status ptp_mesh_create(const float *xyz, int64_t n_verts, const int32_t *faces, int64_t n_faces,
+                           int ptr_kind, void *stream, ptp_mesh **out);
+
+/* Bounding-box diagonal of the vertices (the "mesh diameter" used for error
+ * tolerances), vertex and face counts.  Any output pointer may be NULL. */
+ptp_status ptp_mesh_info(const ptp_mesh *mesh, int64_t *n_verts, int64_t *n_faces, double *diameter);
+
+/* Release the mesh.  Destroy every ptp_toplesets_t made from it first. */
+ptp_status ptp_mesh_destroy(ptp_mesh *mesh);
+
+/*
+ * Toplesets from the source set S (Sec. 3.1, Definition: V_0 = S and V_r the
+ * not yet visited neighbours of V_{r-1}), computed by a breadth-first search
+ * on the device, and the mesh renumbered so that V_0, V_1, ... occupy
+ * consecutive index ranges (Sec. 3.3, reordering for coalesced access).
+ *  sources  [m] int32 vertex indices, m >= 1; duplicates are allowed.
+ *  PTP_ERR_INDEX if a source is outside [0, n_verts); PTP_ERR_ARG if m < 1.
+ *  Vertices not reachable from S are placed after the last topleset and get
+ *  +inf from ptp_distance.  The order inside one topleset is unspecified.
+ *  Asynchronous apart from the source validation, which reads the sources
+ *  on the host (a device `sources` array is copied to the host first).
+ *  The mesh must outlive the returned handle.
+ */
+ptp_status ptp_toplesets(ptp_mesh *mesh, const int32_t *sources, int32_t m, int ptr_kind, void *stream,
+                         ptp_toplesets_t **out);
+
+/*
+ * Topleset layout, for inspection.  Blocks on `stream`.  Outputs (any may be
+ * NULL): rho, the number of toplesets; n_reached, the vertices reachable
+ * from S; off_dev, device array [rho + 1] of topleset start offsets in the
+ * renumbered order; perm_dev, device array [n_verts] mapping renumbered
+ * index -> original index.  The device arrays belong to the handle.
+ */
+ptp_status ptp_toplesets_info(ptp_toplesets_t *tops, void *stream, int32_t *rho, int32_t *n_reached,
+                              const int32_t **off_dev, const int32_t **perm_dev);
+
+ptp_status ptp_toplesets_destroy(ptp_toplesets_t *tops);
+
+/*
+ * PTP (Sec. 3.2): d_0 = +inf except d_0(S) = 0; iteration k recomputes, from
+ * d_{k-1} only, every non-source vertex of the band
+ * B = V_{i_{k-1}} u ... u V_{j_k} as the minimum of its old value and the
+ * update step (Sec. 2.2, planar Eikonal solve under the monotonicity
+ * condition Q X^T n < 0, else the edge fallback) over its incident
+ * triangles; j_k = min(k, rho - 1) (Eq. upper_band) and i_k = i_{k-1} + 1
+ * when every vertex of V_{i_{k-1}} passed the relative-change test
+ * (Eq. lower_band); the run stops when i_k > rho - 1.
+ *  d_out   caller-owned DEVICE buffer of n_verts float32, ORIGINAL order;
+ *          unreachable vertices get +inf.
+ *  stats   NULL: fully asynchronous.  Non-NULL: blocks on `stream` and fills
+ *          the statistics; the return value is then the device-side status
+ *          (PTP_OK, PTP_ERR_NOT_CONVERGED with d_out written, or
+ *          PTP_ERR_TIMEOUT).
+ * Per-call scratch (two distance buffers, per-vertex change stamps) is a
+ * stream-ordered allocation released on `stream` before returning.
+ * Calls on the same handle must not overlap in time.
+ */
+ptp_status ptp_distance(ptp_toplesets_t *tops, const ptp_params *params, float *d_out, void *stream,
+                        ptp_stats *stats);
+
+/* Statistics of the last ptp_distance call on this handle.  Blocks on
+ * `stream`.  Returns that call's device-side status. */
+ptp_status ptp_last_stats(ptp_toplesets_t *tops, void *stream, ptp_stats *stats);
+
+/*
+ * All stages in one call: mesh, toplesets, distance, then release.
+ *  ptr_kind applies to xyz, faces, sources AND d_out (host d_out is filled
+ *  by a device-to-host copy before returning).  Blocks on `stream`.
+ */
+ptp_status ptp_geodesic(const float *xyz, int64_t n_verts, const int32_t *faces, int64_t n_faces,
+                        const int32_t *sources, int32_t m, int ptr_kind, const ptp_params *params,
+                        float *d_out, void *stream, ptp_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTP_H */
