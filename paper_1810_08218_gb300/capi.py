@@ -1,0 +1,299 @@
+"""Thin Python binding of the C ABI in include/ptp.h (ctypes).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library libptp.so.  Tensors are torch CUDA tensors (device memory) or numpy
+arrays (host memory); streams are torch.cuda.Stream objects or None for the
+current stream.  The library must have been built (build.build()); loading
+fails loudly otherwise -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PTP_OK = 0
+PTP_ERR_ARG = 1
+PTP_ERR_INDEX = 2
+PTP_ERR_DEGENERATE_FACE = 3
+PTP_ERR_CUDA = 4
+PTP_ERR_NOT_CONVERGED = 5
+PTP_ERR_TIMEOUT = 6
+PTP_ERR_NOMEM = 7
+PTP_ERR_TOO_LARGE = 8
+
+PTP_HOST = 0
+PTP_DEVICE = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PTPError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("eps_abs", ctypes.c_double), ("max_iter", ctypes.c_int64),
+                ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("trace", ctypes.c_void_p),
+                ("trace_cap", ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("band_updates", ctypes.c_int64), ("active_updates", ctypes.c_int64),
+                ("changed", ctypes.c_int64), ("fp64_solves", ctypes.c_int64), ("rho", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+TRACE_DTYPE = np.dtype([("i", np.int32), ("j", np.int32), ("active", np.int32), ("changed", np.int32),
+                        ("maxrel", np.float32), ("advanced", np.int32), ("errsum", np.float64)])
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libptp.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or _build.LIB
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} is missing (run paper_1810_08218_gb300.build.build())")
+        lib = ctypes.CDLL(p)
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        i32 = ctypes.c_int32
+        st = ctypes.c_int
+        sig = {
+            "ptp_status_str": (ctypes.c_char_p, [st]),
+            "ptp_params_default": (st, [P]),
+            "ptp_mesh_create": (st, [P, i64, P, i64, ctypes.c_int, P, P]),
+            "ptp_mesh_info": (st, [P, P, P, P]),
+            "ptp_mesh_destroy": (st, [P]),
+            "ptp_toplesets": (st, [P, P, i32, ctypes.c_int, P, P]),
+            "ptp_toplesets_info": (st, [P, P, P, P, P, P]),
+            "ptp_toplesets_destroy": (st, [P]),
+            "ptp_distance": (st, [P, P, P, P, P]),
+            "ptp_last_stats": (st, [P, P, P]),
+            "ptp_geodesic": (st, [P, i64, P, i64, P, i32, ctypes.c_int, P, P, P, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_str(code: int) -> str:
+    try:
+        return load().ptp_status_str(int(code)).decode()
+    except Exception:
+        return f"status {code}"
+
+
+def _check(code: int, where: str, ok=(PTP_OK,)):
+    if code not in ok:
+        raise PTPError(code, where)
+    return code
+
+
+# --------------------------------------------------------------------------
+# marshalling helpers
+# --------------------------------------------------------------------------
+
+def _stream_ptr(stream) -> int | None:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) or None
+
+
+def _array_arg(x, dtype):
+    """(pointer, ptr_kind, keepalive) for a torch CUDA tensor or a host array."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        tdt = {np.float32: torch.float32, np.int32: torch.int32}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            x = x.to(tdt).contiguous()
+        kind = PTP_DEVICE if x.is_cuda else PTP_HOST
+        return ctypes.c_void_p(x.data_ptr()), kind, x
+    a = np.ascontiguousarray(np.asarray(x), dtype=dtype)
+    return a.ctypes.data_as(ctypes.c_void_p), PTP_HOST, a
+
+
+class _DevView:
+    """Exposes a device pointer through __cuda_array_interface__ so torch can
+    wrap it without a copy (the owning handle must stay alive)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 3,
+                                         "strides": None}
+        self._owner = owner
+
+
+# --------------------------------------------------------------------------
+# handles
+# --------------------------------------------------------------------------
+
+class Mesh:
+    def __init__(self, handle: ctypes.c_void_p, n: int, nf: int, diameter: float):
+        self.handle = handle
+        self.n = n
+        self.nf = nf
+        self.diameter = diameter
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                ptp_mesh_destroy(self)
+            except Exception:
+                pass
+
+
+class Toplesets:
+    def __init__(self, handle: ctypes.c_void_p, mesh: Mesh):
+        self.handle = handle
+        self.mesh = mesh  # keeps the mesh alive
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                ptp_toplesets_destroy(self)
+            except Exception:
+                pass
+
+
+# --------------------------------------------------------------------------
+# the C ABI, same names
+# --------------------------------------------------------------------------
+
+def ptp_params_default(**overrides) -> Params:
+    p = Params()
+    _check(load().ptp_params_default(ctypes.byref(p)), "ptp_params_default")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def ptp_mesh_create(xyz, faces, stream=None) -> Mesh:
+    lib = load()
+    px, kx, kx_keep = _array_arg(xyz, np.float32)
+    pf, kf, kf_keep = _array_arg(faces, np.int32)
+    if kx != kf:
+        raise ValueError("xyz and faces must both be host arrays or both device tensors")
+    n = int(np.prod(kx_keep.shape)) // 3
+    nf = int(np.prod(kf_keep.shape)) // 3
+    h = ctypes.c_void_p()
+    _check(lib.ptp_mesh_create(px, n, pf, nf, kx, _stream_ptr(stream), ctypes.byref(h)), "ptp_mesh_create")
+    d = ctypes.c_double()
+    lib.ptp_mesh_info(h, None, None, ctypes.byref(d))
+    return Mesh(h, n, nf, d.value)
+
+
+def ptp_mesh_info(mesh: Mesh) -> tuple[int, int, float]:
+    n = ctypes.c_int64()
+    nf = ctypes.c_int64()
+    d = ctypes.c_double()
+    _check(load().ptp_mesh_info(mesh.handle, ctypes.byref(n), ctypes.byref(nf), ctypes.byref(d)), "ptp_mesh_info")
+    return n.value, nf.value, d.value
+
+
+def ptp_mesh_destroy(mesh: Mesh) -> None:
+    if mesh.handle:
+        h, mesh.handle = mesh.handle, None
+        _check(load().ptp_mesh_destroy(h), "ptp_mesh_destroy")
+
+
+def ptp_toplesets(mesh: Mesh, sources, stream=None) -> Toplesets:
+    lib = load()
+    ps, ks, keep = _array_arg(sources, np.int32)
+    m = int(np.prod(keep.shape))
+    h = ctypes.c_void_p()
+    _check(lib.ptp_toplesets(mesh.handle, ps, m, ks, _stream_ptr(stream), ctypes.byref(h)), "ptp_toplesets")
+    return Toplesets(h, mesh)
+
+
+def ptp_toplesets_info(tops: Toplesets, stream=None) -> dict:
+    """rho, n_reached and (as torch int32 CUDA tensors viewing the handle's
+    memory) the topleset offsets [rho+1] and the permutation [n]."""
+    import torch
+
+    rho = ctypes.c_int32()
+    nr = ctypes.c_int32()
+    off = ctypes.c_void_p()
+    perm = ctypes.c_void_p()
+    _check(load().ptp_toplesets_info(tops.handle, _stream_ptr(stream), ctypes.byref(rho), ctypes.byref(nr),
+                                     ctypes.byref(off), ctypes.byref(perm)), "ptp_toplesets_info")
+    offt = torch.as_tensor(_DevView(off.value, rho.value + 1, "<i4", tops), device="cuda")
+    permt = torch.as_tensor(_DevView(perm.value, tops.mesh.n, "<i4", tops), device="cuda")
+    return {"rho": rho.value, "n_reached": nr.value, "off": offt, "perm": permt}
+
+
+def ptp_toplesets_destroy(tops: Toplesets) -> None:
+    if tops.handle:
+        h, tops.handle = tops.handle, None
+        _check(load().ptp_toplesets_destroy(h), "ptp_toplesets_destroy")
+
+
+def ptp_distance(tops: Toplesets, params: Params, d_out, stream=None, stats: bool = True,
+                 ok=(PTP_OK,)) -> dict | None:
+    """Fill d_out (torch float32 CUDA tensor [n], original vertex order).
+    With stats=True the call blocks and returns the run statistics."""
+    st = Stats() if stats else None
+    code = load().ptp_distance(tops.handle, ctypes.byref(params), ctypes.c_void_p(d_out.data_ptr()),
+                               _stream_ptr(stream), ctypes.byref(st) if st is not None else None)
+    _check(code, "ptp_distance", ok)
+    return st.as_dict() if st is not None else None
+
+
+def ptp_last_stats(tops: Toplesets, stream=None) -> dict:
+    st = Stats()
+    load().ptp_last_stats(tops.handle, _stream_ptr(stream), ctypes.byref(st))
+    return st.as_dict()
+
+
+def ptp_geodesic(xyz, faces, sources, params: Params, d_out, stream=None, ok=(PTP_OK,)) -> dict:
+    """Whole pipeline in one call.  All arrays must be of one kind: host
+    (numpy / CPU tensors, d_out a writable float32 host array) or device."""
+    lib = load()
+    px, kx, kx_keep = _array_arg(xyz, np.float32)
+    pf, kf, kf_keep = _array_arg(faces, np.int32)
+    ps, ks, ks_keep = _array_arg(sources, np.int32)
+    try:
+        import torch
+        is_t = isinstance(d_out, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        is_t = False
+    if is_t:
+        pd, kd = ctypes.c_void_p(d_out.data_ptr()), (PTP_DEVICE if d_out.is_cuda else PTP_HOST)
+    else:
+        if not (isinstance(d_out, np.ndarray) and d_out.dtype == np.float32 and d_out.flags.c_contiguous):
+            raise ValueError("host d_out must be a contiguous float32 numpy array")
+        pd, kd = d_out.ctypes.data_as(ctypes.c_void_p), PTP_HOST
+    if len({kx, kf, ks, kd}) != 1:
+        raise ValueError("xyz, faces, sources and d_out must all be host or all device")
+    n = int(np.prod(kx_keep.shape)) // 3
+    nf = int(np.prod(kf_keep.shape)) // 3
+    m = int(np.prod(ks_keep.shape))
+    st = Stats()
+    code = lib.ptp_geodesic(px, n, pf, nf, ps, m, kx, ctypes.byref(params), pd, _stream_ptr(stream),
+                            ctypes.byref(st))
+    _check(code, "ptp_geodesic", ok)
+    return st.as_dict()

@@ -1,0 +1,552 @@
+// The PTP iteration (Sec. 3.2) over the sliding update band, as one
+// persistent cooperative kernel with the window control on the device.
+//
+// Iteration k recomputes every non-source vertex of the band
+// B = V_{i_{k-1}} u ... u V_{j_k} from d_{k-1} (Jacobi: two distance buffers,
+// read d_{k-1}, write d_k), then a grid barrier, then every CTA applies
+// Eq. lower_band from a per-iteration "some vertex of V_{i_{k-1}} failed the
+// relative-change test" flag; j_k = min(k, rho - 1) is Eq. upper_band.
+//
+// Work skipping (exact): a vertex's new value depends only on its own and its
+// neighbours' previous values, so when no neighbour changed in iteration k-1
+// its recomputation would return d_{k-1}(u) unchanged.  Every vertex that
+// changes stamps its neighbours with k (nstamp); only vertices stamped k-1,
+// or entering the band, are recomputed.  Distances of skipped vertices that
+// changed in k-1 are copied forward so both buffers stay Jacobi-consistent.
+//
+// The update step (Sec. 2.2) is evaluated in FP32 in a form shifted by d1
+// (the unknown is q = p - d1, a local quantity of the order of an edge), with
+// the discriminant written as det * (L - |d2-d1|) (L + |d2-d1|), L = |x2-x1|,
+// so neither the magnitude of d nor the front's alignment with an edge
+// cancels digits.  Near-degenerate triangles (some angle with squared sine
+// below 1e-6) and the rare residual cancellation are solved in FP64.  The
+// relative-change test of Eq. lower_band is evaluated in FP64.
+#include <math.h>
+#include <stdlib.h>
+
+#include "ptp_internal.cuh"
+
+namespace {
+
+constexpr int DIST_THREADS = 512;
+#define INF __int_as_float(0x7f800000)
+
+struct DistArgs {
+    const float4 *__restrict__ pos;
+    const int4 *__restrict__ ring;
+    const int *__restrict__ meta;
+    const int *__restrict__ row;
+    const int2 *__restrict__ pairs;
+    const int *__restrict__ off;
+    const int *__restrict__ info;
+    float *d0;
+    float *d1;
+    int *nstamp;
+    int *chg;
+    ptp_ctrl *ctrl;
+    ptp_trace_rec *trace;
+    long long trace_cap;
+    double eps;
+    double eps_abs;
+    long long max_iter;
+};
+
+__device__ __forceinline__ float fsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// FP64 solve of the planar update for vertex x0 of triangle (x0, x1, x2),
+// given e1 = x1 - x0, e2 = x2 - x0 (FP32 differences of nearby coordinates,
+// exact or nearly so) and finite d1, d2.
+__device__ __noinline__ float tri_solve_fp64(float3 e1f, float3 e2f, float d1f, float d2f, float fb) {
+    const double e1x = e1f.x, e1y = e1f.y, e1z = e1f.z;
+    const double e2x = e2f.x, e2y = e2f.y, e2z = e2f.z;
+    const double a = e1x * e1x + e1y * e1y + e1z * e1z;
+    const double c = e2x * e2x + e2y * e2y + e2z * e2z;
+    const double b = e1x * e2x + e1y * e2y + e1z * e2z;
+    const double cx = e1y * e2z - e1z * e2y, cy = e1z * e2x - e1x * e2z, cz = e1x * e2y - e1y * e2x;
+    const double det = cx * cx + cy * cy + cz * cz;
+    if (!(det > 1e-12 * a * c)) return fb;
+    const double fx = e2x - e1x, fy = e2y - e1y, fz = e2z - e1z;  // x2 - x1
+    const double A = fx * fx + fy * fy + fz * fz;
+    const double d1 = d1f, delta = (double)d2f - d1;
+    const double L = sqrt(A), ad = fabs(delta);
+    if (!(ad < L)) return fb;
+    const double disc = (L - ad) * (L + ad);
+    const double amb = -(e1x * fx + e1y * fy + e1z * fz);  // a - b
+    const double cmb = e2x * fx + e2y * fy + e2z * fz;     // c - b
+    const double q = (delta * amb + sqrt(det * disc)) / A;
+    if (cmb * q + b * delta > 0.0 && amb * q - a * delta > 0.0) {
+        const float p = (float)(d1 + q);
+        return p < fb ? p : fb;
+    }
+    return fb;
+}
+
+// Update step (Sec. 2.2) for vertex x0 from triangle (x0, x1, x2), with
+// e1 = x1 - x0, e2 = x2 - x0, a1 = |e1|^2, l1 = |e1|, likewise a2, l2.
+// Returns the candidate distance: the planar solution when it exists and
+// satisfies the monotonicity condition Q X^T n < 0, else
+// min(d1 + l1, d2 + l2).
+__device__ __forceinline__ float tri_update(float3 e1, float3 e2, float d1, float d2, float a1, float l1, float a2,
+                                            float l2, unsigned &nfp64) {
+    const float fb = fminf(d1 + l1, d2 + l2);
+    if (!(fmaxf(d1, d2) < INF)) return fb;  // at most one finite neighbour: edge only
+    const float3 e12 = sub3(e2, e1);
+    const float b = dot3(e1, e2);
+    const float3 cr = cross3(e1, e2);
+    const float det = dot3(cr, cr);
+    const float A = dot3(e12, e12);
+    const float big = fmaxf(a1 * a2, A * fmaxf(a1, a2));
+    const float delta = d2 - d1;
+    const float ad = fabsf(delta);
+    const float L = fsqrt(A);
+    if (det < 1e-6f * big) {
+        ++nfp64;
+        return tri_solve_fp64(e1, e2, d1, d2, fb);
+    }
+    if (!(ad < L)) return fb;
+    const float disc = (L - ad) * (L + ad);
+    if (disc < 0x1p-20f * A) {
+        ++nfp64;
+        return tri_solve_fp64(e1, e2, d1, d2, fb);
+    }
+    const float amb = -dot3(e1, e12);  // a - b
+    const float cmb = dot3(e2, e12);   // c - b
+    const float q = __fdividef(fmaf(delta, amb, fsqrt(det * disc)), A);
+    const bool causal = (fmaf(cmb, q, b * delta) > 0.0f) && (fmaf(amb, q, -a1 * delta) > 0.0f);
+    return causal ? fminf(d1 + q, fb) : fb;
+}
+
+__device__ __forceinline__ float3 xyz(float4 p) { return make_float3(p.x, p.y, p.z); }
+
+// New value of a ring-slot vertex: min of the old value and the update over
+// its fan.  All neighbour loads are issued first (one dependent round trip);
+// the edge lengths roll along the fan.  Triangles whose two neighbours are
+// both no closer than the current best are skipped: the update never
+// returns less than min(d1, d2).
+__device__ __forceinline__ float update_ring(const DistArgs &a, const int ids[PTP_RING], float3 x0, int m, float best,
+                                             const float *__restrict__ dp, unsigned &nfp64) {
+    float3 e[PTP_RING];
+    float dn[PTP_RING];
+#pragma unroll
+    for (int t = 0; t < PTP_RING; ++t) {
+        if (t < m) {
+            e[t] = sub3(xyz(__ldg(a.pos + ids[t])), x0);
+            dn[t] = __ldcg(dp + ids[t]);
+        } else {
+            e[t] = make_float3(0.0f, 0.0f, 0.0f);
+            dn[t] = INF;
+        }
+    }
+    float a_prev = dot3(e[0], e[0]);
+    float l_prev = fsqrt(a_prev);
+#pragma unroll
+    for (int t = 0; t < PTP_RING - 1; ++t) {
+        const float a_next = dot3(e[t + 1], e[t + 1]);
+        const float l_next = fsqrt(a_next);
+        if (t < m - 1 && fminf(dn[t], dn[t + 1]) < best) {
+            const float c = tri_update(e[t], e[t + 1], dn[t], dn[t + 1], a_prev, l_prev, a_next, l_next, nfp64);
+            best = fminf(best, c);
+        }
+        a_prev = a_next;
+        l_prev = l_next;
+    }
+    return best;
+}
+
+// New value of a GENERAL vertex from its corner list.
+__device__ __noinline__ float update_general(const DistArgs &a, int u, float best, const float *__restrict__ dp,
+                                             unsigned &nfp64) {
+    const float3 x0 = xyz(__ldg(a.pos + u));
+    const int cb = __ldg(a.row + u), ce = __ldg(a.row + u + 1);
+    for (int c = cb; c < ce; ++c) {
+        const int2 pr = __ldg(a.pairs + c);
+        const float d1 = __ldcg(dp + pr.x), d2 = __ldcg(dp + pr.y);
+        if (!(fminf(d1, d2) < best)) continue;
+        const float3 e1 = sub3(xyz(__ldg(a.pos + pr.x)), x0), e2 = sub3(xyz(__ldg(a.pos + pr.y)), x0);
+        const float a1 = dot3(e1, e1), a2 = dot3(e2, e2);
+        best = fminf(best, tri_update(e1, e2, d1, d2, a1, fsqrt(a1), a2, fsqrt(a2), nfp64));
+    }
+    return best;
+}
+
+__device__ __noinline__ void stamp_general(const DistArgs &a, int u, int k) {
+    const int cb = __ldg(a.row + u), ce = __ldg(a.row + u + 1);
+    for (int c = cb; c < ce; ++c) {
+        const int2 pr = __ldg(a.pairs + c);
+        a.nstamp[pr.x] = k;
+        a.nstamp[pr.y] = k;
+    }
+}
+
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+#ifndef PTP_DIST_MIN_BLOCKS
+#define PTP_DIST_MIN_BLOCKS 1
+#endif
+
+// Band bounds of one iteration.
+struct Band {
+    int copy_lo;  // start of the topleset retired after the previous iteration
+    int lo;       // off[i]
+    int vi_end;   // off[i + 1]
+    int vj_beg;   // off[j]
+    int hi;       // off[j + 1]
+};
+
+// The persistent window kernel.  Work is dealt out in chunks of 32
+// consecutive renumbered vertices (coalesced), chunk c to warp c mod W with
+// the warps numbered across CTAs first, so even a narrow band spreads over
+// all SMs.  Everything indexed by the vertex itself is loaded in one round
+// trip before deciding whether to recompute it, and the next iteration's
+// band bounds are fetched before the barrier, so after the barrier only the
+// neighbours' distances are on the critical path.
+__global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(DistArgs a) {
+    const int rho = __ldcg(a.info);
+    const int nsrc = __ldcg(a.off + 1);
+    const long long max_iter = a.max_iter > 0 ? a.max_iter : 8LL * rho + 64;
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int nwarps = (blockDim.x >> 5) * gridDim.x;
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned tot_active = 0, tot_changed = 0, nfp64 = 0;
+    unsigned long long prev_hi[2] = {0ull, 0ull};
+    long long band_updates = 0;
+    int i = 0;  // i_{k-1}
+    long long k = 1;
+    int status = PTP_ERR_NOT_CONVERGED;
+    __shared__ float s_max[DIST_THREADS / 32];
+    __shared__ double s_sum[DIST_THREADS / 32];
+    __shared__ int s_cnt[2][DIST_THREADS / 32];
+
+    auto off_at = [&](int r) { return __ldcg(a.off + (r < rho ? r : rho)); };
+    Band bd;  // iteration 1: i_0 = 0, j_1 = min(1, rho - 1)
+    {
+        const int j1 = rho > 1 ? 1 : 0;
+        bd.lo = 0;
+        bd.copy_lo = 0;
+        bd.vi_end = off_at(1);
+        bd.vj_beg = off_at(j1);
+        bd.hi = off_at(j1 + 1);
+    }
+
+    for (; k <= max_iter; ++k) {
+        const int j = k < rho ? (int)k : rho - 1;
+        const float *dp = (k & 1) ? a.d0 : a.d1;  // d_{k-1} lives in buffer (k-1) % 2
+        float *dnx = (k & 1) ? a.d1 : a.d0;
+        const bool entering = (long long)j == k;
+        const int first = bd.lo > nsrc ? bd.lo : nsrc;
+        const int start = bd.copy_lo < first ? bd.copy_lo : first;
+
+        int notconv = 0, n_active = 0, n_changed = 0;
+        float maxrel = 0.0f;
+        double errsum = 0.0;
+        const int base = start & ~31;
+        for (int c = gwarp;; c += nwarps) {
+            const int u = base + c * 32 + lane;
+            if (u - lane >= bd.hi) break;
+            if (u < start || u >= bd.hi) continue;
+            if (u < bd.lo) {  // retired after the previous iteration: keep both buffers equal
+                dnx[u] = __ldcg(dp + u);
+                continue;
+            }
+            if (u < nsrc) continue;  // sources stay 0
+            const float dold = __ldcg(dp + u);
+            const int ns = __ldcg(a.nstamp + u);
+            const int cg = __ldcg(a.chg + u);
+            const int meta = __ldg(a.meta + u);
+            const int4 r0 = __ldg(a.ring + 2 * u), r1 = __ldg(a.ring + 2 * u + 1);
+            const float3 x0 = xyz(__ldg(a.pos + u));
+            const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            const bool need = (entering && u >= bd.vj_beg) || ns >= k - 1;
+            float dnew = dold;
+            if (need) {
+                if (meta & PTP_META_GENERAL) dnew = update_general(a, u, dold, dp, nfp64);
+                else dnew = update_ring(a, ids, x0, meta & PTP_META_CNT, dold, dp, nfp64);
+                ++n_active;
+            }
+            if (need || cg == k - 1) dnx[u] = dnew;
+            if (dnew != dold) {
+                ++n_changed;
+                a.chg[u] = (int)k;
+                if (meta & PTP_META_GENERAL) {
+                    stamp_general(a, u, (int)k);
+                } else {
+                    const int cnt = meta & PTP_META_CNT;
+#pragma unroll
+                    for (int t = 0; t < PTP_RING; ++t)
+                        if (t < cnt) a.nstamp[ids[t]] = (int)k;
+                }
+            }
+            if (u < bd.vi_end) {
+                // relative-change test of Eq. lower_band, in FP64
+                const double o = dold, w = dnew, delta = fabs(w - o);
+                const bool ok = isfinite(o) && (delta == 0.0 || delta < a.eps * o + a.eps_abs);
+                if (!ok) notconv = 1;
+                const double rel = isfinite(o) ? (o > 0.0 ? delta / o : 0.0) : (double)INF;
+                maxrel = fmaxf(maxrel, (float)rel);
+                errsum += rel;
+            }
+        }
+        tot_active += n_active;
+        tot_changed += n_changed;
+
+        if (a.trace && k - 1 < a.trace_cap) {
+            const float wm = warp_max_f(maxrel);
+            const double ws = warp_sum_d(errsum);
+            const int wa = warp_sum_i(n_active), wc = warp_sum_i(n_changed);
+            const int wid = threadIdx.x >> 5;
+            if (lane == 0) {
+                s_max[wid] = wm;
+                s_sum[wid] = ws;
+                s_cnt[0][wid] = wa;
+                s_cnt[1][wid] = wc;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float bm = 0.0f;
+                double bs = 0.0;
+                int ba = 0, bc = 0;
+                for (int w = 0; w < DIST_THREADS / 32; ++w) {
+                    bm = fmaxf(bm, s_max[w]);
+                    bs += s_sum[w];
+                    ba += s_cnt[0][w];
+                    bc += s_cnt[1][w];
+                }
+                ptp_trace_rec *rec = a.trace + (k - 1);
+                if (ba) atomicAdd(&rec->active, ba);
+                if (bc) atomicAdd(&rec->changed, bc);
+                if (bs != 0.0) atomicAdd(&rec->errsum, bs);
+                if (bm > 0.0f) atomicMax((int *)&rec->maxrel, __float_as_int(bm));
+            }
+        }
+
+        // the bounds the next iteration may need are static: fetch them now
+        const int jn = k + 1 < rho ? (int)(k + 1) : rho - 1;
+        const int o_i2 = off_at(i + 2);
+        const int o_jn = off_at(jn), o_jn1 = off_at(jn + 1);
+
+        const int any = __syncthreads_or(notconv);
+        const long long failed = ptp_grid_sync(a.ctrl->bar, k, any ? 1u : 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi);
+        if (failed < 0) {
+            status = PTP_ERR_TIMEOUT;
+            break;
+        }
+        if (leader) {
+            band_updates += bd.hi - first;
+            if (a.trace && k - 1 < a.trace_cap) {
+                ptp_trace_rec *rec = a.trace + (k - 1);
+                rec->i = i;
+                rec->j = j;
+                rec->advanced = failed ? 0 : 1;
+            }
+        }
+        if (!failed) {
+            // Eq. lower_band: i_k = i_{k-1} + 1; V_{i_{k-1}} retires and is
+            // copied forward in the next iteration (V_0 never changes)
+            ++i;
+            if (i > rho - 1) {
+                status = PTP_OK;
+                break;
+            }
+            bd.copy_lo = i >= 2 ? bd.lo : bd.vi_end;
+            bd.lo = bd.vi_end;
+            bd.vi_end = o_i2;
+        } else {
+            bd.copy_lo = bd.lo;
+        }
+        bd.vj_beg = o_jn;
+        bd.hi = o_jn1;
+    }
+    if (status == PTP_ERR_NOT_CONVERGED) k = max_iter;
+
+    // per-CTA totals
+    __shared__ unsigned long long s_tot[3];
+    if (threadIdx.x == 0) s_tot[0] = s_tot[1] = s_tot[2] = 0ull;
+    __syncthreads();
+    if (tot_active) atomicAdd(&s_tot[0], (unsigned long long)tot_active);
+    if (tot_changed) atomicAdd(&s_tot[1], (unsigned long long)tot_changed);
+    if (nfp64) atomicAdd(&s_tot[2], (unsigned long long)nfp64);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&a.ctrl->active, s_tot[0]);
+        atomicAdd(&a.ctrl->changed, s_tot[1]);
+        atomicAdd(&a.ctrl->fp64, s_tot[2]);
+    }
+    if (leader) {
+        a.ctrl->iterations = k;
+        a.ctrl->band_updates = band_updates;
+        if (status != PTP_ERR_TIMEOUT) atomicCAS(&a.ctrl->status, 0, status);
+    }
+}
+
+__global__ void init_distances(const int *__restrict__ off, int n, float *__restrict__ d0, float *__restrict__ d1,
+                               int *__restrict__ nstamp, int *__restrict__ chg) {
+    const int nsrc = off[1];
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const float v = u < nsrc ? 0.0f : INF;
+        d0[u] = v;
+        d1[u] = v;
+        nstamp[u] = -2;
+        chg[u] = -2;
+    }
+}
+
+// d_out[perm[u]] = d_K[u]; the final iterate lives in buffer K % 2.
+__global__ void scatter_out(const int *__restrict__ perm, int n, const float *__restrict__ d0, const float *__restrict__ d1,
+                            const ptp_ctrl *__restrict__ ctrl, float *__restrict__ out) {
+    const float *d = (ctrl->iterations & 1) ? d1 : d0;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) out[perm[u]] = d[u];
+}
+
+unsigned blocks_for(int64_t work, int threads, int device) {
+    int64_t b = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)ptp_num_sms(device) * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+extern "C" ptp_status ptp_last_stats(ptp_toplesets_t *t, void *stream, ptp_stats *st) {
+    if (!t || !st) return PTP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    ptp_ctrl h;
+    int info[4];
+    PTP_TRY(cudaMemcpyAsync(&h, t->ctrl, sizeof(ptp_ctrl), cudaMemcpyDeviceToHost, s));
+    PTP_TRY(cudaMemcpyAsync(info, t->info, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    PTP_TRY(cudaStreamSynchronize(s));
+    st->iterations = h.iterations;
+    st->band_updates = h.band_updates;
+    st->active_updates = (int64_t)h.active;
+    st->changed = (int64_t)h.changed;
+    st->fp64_solves = (int64_t)h.fp64;
+    st->rho = info[0];
+    st->status = h.status;
+    return (ptp_status)h.status;
+}
+
+extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params, float *d_out, void *stream,
+                                   ptp_stats *stats) {
+    if (!t || !params || !d_out) return PTP_ERR_ARG;
+    if (!(params->eps >= 0.0) || !(params->eps_abs >= 0.0) || params->max_iter < 0 || params->trace_cap < 0)
+        return PTP_ERR_ARG;
+    if (params->block != 0 && params->block != DIST_THREADS) return PTP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = t->n;
+    const int dev = t->device;
+
+    float *dbuf = nullptr;
+    int *ibuf = nullptr;
+    PTP_TRY(cudaMallocAsync((void **)&dbuf, sizeof(float) * 2 * n, s));
+    cudaError_t ce = cudaMallocAsync((void **)&ibuf, sizeof(int) * 2 * n, s);
+    if (ce != cudaSuccess) {
+        cudaFreeAsync(dbuf, s);
+        return ptp_internal_cuda_status(ce);
+    }
+    ptp_status st = PTP_OK;
+    do {
+        ce = cudaMemsetAsync(t->ctrl, 0, sizeof(ptp_ctrl), s);
+        if (ce != cudaSuccess) break;
+        if (params->trace && params->trace_cap > 0) {
+            ce = cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s);
+            if (ce != cudaSuccess) break;
+        }
+        init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->off, (int)n, dbuf, dbuf + n, ibuf, ibuf + n);
+        ce = cudaGetLastError();
+        if (ce != cudaSuccess) break;
+
+        int per_sm = 0;
+        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window, DIST_THREADS, 0);
+        if (ce != cudaSuccess) break;
+        if (per_sm < 1) { st = PTP_ERR_CUDA; break; }
+        int grid = per_sm * ptp_num_sms(dev);
+        if (params->grid > 0 && params->grid < grid) grid = params->grid;
+
+        DistArgs a;
+        a.pos = t->pos;
+        a.ring = t->ring;
+        a.meta = t->meta;
+        a.row = t->row;
+        a.pairs = t->pairs;
+        a.off = t->off;
+        a.info = t->info;
+        a.d0 = dbuf;
+        a.d1 = dbuf + n;
+        a.nstamp = ibuf;
+        a.chg = ibuf + n;
+        a.ctrl = t->ctrl;
+        a.trace = (ptp_trace_rec *)params->trace;
+        a.trace_cap = params->trace ? params->trace_cap : 0;
+        a.eps = params->eps;
+        a.eps_abs = params->eps_abs;
+        a.max_iter = params->max_iter;
+        void *args[] = {(void *)&a};
+        ce = cudaLaunchCooperativeKernel((const void *)ptp_window, dim3(grid), dim3(DIST_THREADS), args, 0, s);
+        if (ce != cudaSuccess) break;
+        scatter_out<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, dbuf, dbuf + n, t->ctrl, d_out);
+        ce = cudaGetLastError();
+    } while (0);
+    cudaFreeAsync(dbuf, s);
+    cudaFreeAsync(ibuf, s);
+    if (ce != cudaSuccess) return ptp_internal_cuda_status(ce);
+    if (st != PTP_OK) return st;
+    if (stats) return ptp_last_stats(t, stream, stats);
+    return PTP_OK;
+}
+
+extern "C" ptp_status ptp_geodesic(const float *xyz, int64_t n_verts, const int32_t *faces, int64_t n_faces,
+                                   const int32_t *sources, int32_t m, int ptr_kind, const ptp_params *params,
+                                   float *d_out, void *stream, ptp_stats *stats) {
+    if (!d_out || !params) return PTP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    ptp_mesh *mesh = nullptr;
+    PTP_CHECK(ptp_mesh_create(xyz, n_verts, faces, n_faces, ptr_kind, stream, &mesh));
+    ptp_toplesets_t *tops = nullptr;
+    ptp_status st = ptp_toplesets(mesh, sources, m, ptr_kind, stream, &tops);
+    if (st != PTP_OK) {
+        ptp_mesh_destroy(mesh);
+        return st;
+    }
+    float *dev_out = d_out;
+    if (ptr_kind == PTP_HOST) {
+        cudaError_t ce = cudaMallocAsync((void **)&dev_out, sizeof(float) * n_verts, s);
+        if (ce != cudaSuccess) {
+            ptp_toplesets_destroy(tops);
+            ptp_mesh_destroy(mesh);
+            return ptp_internal_cuda_status(ce);
+        }
+    }
+    ptp_stats local;
+    st = ptp_distance(tops, params, dev_out, stream, &local);
+    if (ptr_kind == PTP_HOST) {
+        cudaError_t ce = cudaMemcpyAsync(d_out, dev_out, sizeof(float) * n_verts, cudaMemcpyDeviceToHost, s);
+        cudaFreeAsync(dev_out, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess && (st == PTP_OK || st == PTP_ERR_NOT_CONVERGED)) st = ptp_internal_cuda_status(ce);
+    }
+    if (stats) *stats = local;
+    ptp_toplesets_destroy(tops);
+    ptp_mesh_destroy(mesh);
+    return st;
+}

@@ -1,0 +1,160 @@
+// Internal declarations shared by the CUDA translation units of the PTP
+// library.  Nothing here is part of the public ABI (include/ptp.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ptp.h"
+
+#define PTP_TRY(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e__ = (call);                                                        \
+        if (e__ != cudaSuccess) return ptp_internal_cuda_status(e__);                    \
+    } while (0)
+
+#define PTP_CHECK(expr)                                                                  \
+    do {                                                                                 \
+        ptp_status s__ = (expr);                                                         \
+        if (s__ != PTP_OK) return s__;                                                   \
+    } while (0)
+
+ptp_status ptp_internal_cuda_status(cudaError_t e);
+
+// ---------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------
+
+struct ptp_mesh {
+    int device;
+    cudaStream_t stream;  // creating stream; the handle's memory is freed on it
+    int64_t n, nf;
+    float4 *pos;          // [n] xyz, w = 0
+    int *row;             // [n + 1] corner offsets
+    int2 *pairs;          // [3 nf] per corner: the other two vertices of the face,
+                          //        in the face's cyclic order
+    double diameter;      // bounding-box diagonal
+};
+
+// Device control block of one distance run.
+struct ptp_ctrl {
+    unsigned long long bar[2];   // grid-barrier words (ptp_grid_sync)
+    int status;                  // PTP_OK / PTP_ERR_NOT_CONVERGED / PTP_ERR_TIMEOUT
+    int abort;                   // set by a CTA whose wait timed out
+    long long iterations;        // K
+    long long band_updates;      // sum_k |B_k minus S|
+    unsigned long long active;   // recomputed vertex updates
+    unsigned long long changed;  // updates that lowered d
+    unsigned long long fp64;     // triangle solves taken in FP64
+};
+
+// One-ring slot layout of a renumbered vertex: its neighbours in cyclic
+// order in ring[2u], ring[2u+1] (8 int32, -1 padded).  meta[u] holds the
+// entry count m (low 4 bits), CLOSED for a closed fan (then the last entry
+// repeats the first) and GENERAL for vertices not stored this way.  Triangle
+// t of u is (u, ring[t], ring[t+1]) for t < m - 1.  GENERAL vertices (a link
+// that is not one simple path or cycle, or one longer than the slot) are
+// updated from the corner lists (row, pairs).
+#define PTP_RING 8
+#define PTP_META_CNT 0xF
+#define PTP_META_CLOSED 0x10
+#define PTP_META_GENERAL 0x20
+
+struct ptp_toplesets_s {
+    ptp_mesh *mesh;
+    int device;
+    cudaStream_t stream;
+    int64_t n;
+    int64_t ncorner;
+    int *level;      // [n] original order, -1 = unreachable
+    int *perm;       // [n] renumbered -> original
+    int *iperm;      // [n] original -> renumbered
+    int *off;        // [n + 2] topleset offsets in renumbered order, [0 .. rho]
+    int *info;       // [4]: rho, n_reached, bfs status, number of unique sources
+    float4 *pos;     // [n] renumbered positions
+    int *row;        // [n + 1] renumbered corner offsets
+    int2 *pairs;     // [3 nf] renumbered corner pairs
+    int4 *ring;      // [2 n] one-ring slots
+    int *meta;       // [n]
+    ptp_ctrl *ctrl;  // control block of the last ptp_distance run
+};
+
+// ---------------------------------------------------------------------------
+// Helpers shared by the translation units (host side)
+// ---------------------------------------------------------------------------
+
+int ptp_num_sms(int device);
+
+// Exclusive scan of n int32 values: out[0..n] with out[n] = total.
+// `tmp` must hold ptp_scan_tmp_ints(n) ints.
+int64_t ptp_scan_tmp_ints(int64_t n);
+ptp_status ptp_exclusive_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// A wait gives up after this many SM clock cycles (about 4 s at 2 GHz), then
+// flags PTP_ERR_TIMEOUT and the kernel returns.
+#define PTP_WAIT_CYCLES 8000000000LL
+
+__device__ __forceinline__ unsigned long long ptp_ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ptp_atom_add_release_u64(unsigned long long *p, unsigned long long v) {
+    unsigned long long old;
+    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+
+// Grid-wide barrier for a co-resident (cooperative) grid that also sums one
+// value per CTA.  Two 64-bit words alternate between epochs; each CTA adds
+// 1 + (value << 32) with release semantics, and the low half counts
+// arrivals.  A word is reused only two epochs later, which no CTA can reach
+// before every CTA has left this epoch, so all CTAs read the same final
+// word: its high half minus the high half seen at the word's previous use
+// is the sum of this epoch's values.  `prev_hi` (two entries, thread 0 only)
+// carries those previous high halves.  Returns the sum, or -1 when the wait
+// timed out here (PTP_ERR_TIMEOUT is written to *status) or another CTA
+// flagged an abort; the caller must then leave its loop.  epoch starts at 1.
+__device__ __forceinline__ long long ptp_grid_sync(unsigned long long *words, long long epoch, unsigned value,
+                                                   int *abort_flag, int *status, unsigned long long *prev_hi) {
+    __shared__ long long result_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int w = (int)(epoch & 1);
+        unsigned long long *word = words + w;
+        const unsigned target = (unsigned)((epoch + 1) >> 1) * gridDim.x;
+        const unsigned long long add = 1ull + ((unsigned long long)value << 32);
+        unsigned long long v = ptp_atom_add_release_u64(word, add) + add;
+        long long res = 0;
+        if ((unsigned)v < target) {
+            const long long t0 = clock64();
+            unsigned spins = 0;
+            do {
+                v = ptp_ld_acquire_u64(word);
+                if ((unsigned)v >= target) break;
+                if ((++spins & 63u) == 0) {
+                    if (*(volatile int *)abort_flag) { res = -1; break; }
+                    if (clock64() - t0 > PTP_WAIT_CYCLES) {
+                        atomicExch(status, (int)PTP_ERR_TIMEOUT);
+                        atomicExch(abort_flag, 1);
+                        res = -1;
+                        break;
+                    }
+                }
+            } while (true);
+        }
+        if (res == 0) {
+            const unsigned long long hi = v >> 32;
+            res = (long long)(hi - prev_hi[w]);
+            prev_hi[w] = hi;
+        }
+        result_s = res;
+    }
+    __syncthreads();
+    return result_s;
+}

@@ -1,0 +1,351 @@
+// Mesh construction: validation, the vertex -> incident-triangle lists
+// ("corner lists"), positions and the bounding-box diameter.  The paper keeps
+// the mesh as a compact half-edge structure (Sec. 3.3); the update step only
+// needs, per vertex, the triangles around it, which is what this builds.
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "ptp_internal.cuh"
+
+ptp_status ptp_internal_cuda_status(cudaError_t e) {
+    cudaGetLastError();  // clear a sticky launch error so later calls can proceed
+    return e == cudaErrorMemoryAllocation ? PTP_ERR_NOMEM : PTP_ERR_CUDA;
+}
+
+extern "C" const char *ptp_status_str(ptp_status s) {
+    switch (s) {
+        case PTP_OK: return "PTP_OK";
+        case PTP_ERR_ARG: return "PTP_ERR_ARG";
+        case PTP_ERR_INDEX: return "PTP_ERR_INDEX";
+        case PTP_ERR_DEGENERATE_FACE: return "PTP_ERR_DEGENERATE_FACE";
+        case PTP_ERR_CUDA: return "PTP_ERR_CUDA";
+        case PTP_ERR_NOT_CONVERGED: return "PTP_ERR_NOT_CONVERGED";
+        case PTP_ERR_TIMEOUT: return "PTP_ERR_TIMEOUT";
+        case PTP_ERR_NOMEM: return "PTP_ERR_NOMEM";
+        case PTP_ERR_TOO_LARGE: return "PTP_ERR_TOO_LARGE";
+    }
+    return "PTP_ERR_UNKNOWN";
+}
+
+extern "C" ptp_status ptp_params_default(ptp_params *p) {
+    if (!p) return PTP_ERR_ARG;
+    p->eps = 1e-3;
+    p->eps_abs = 0.0;
+    p->max_iter = 0;
+    p->block = 0;
+    p->grid = 0;
+    p->trace = nullptr;
+    p->trace_cap = 0;
+    return PTP_OK;
+}
+
+int ptp_num_sms(int device) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    return v > 0 ? v : 1;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan (three passes: tile sums, scan of the tile sums, tiles)
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ int block_exclusive_scan(int v, int *excl) {
+    __shared__ int warp_tot[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        int t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;  // inclusive warp totals
+    }
+    __syncthreads();
+    const int before = wid > 0 ? warp_tot[wid - 1] : 0;
+    *excl = before + x - v;
+    const int total = warp_tot[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_tile_sums(const int *__restrict__ in, int64_t n,
+                                                               int *__restrict__ sums) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int s = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q)
+        if (base + q < n) s += in[base + q];
+    int excl;
+    const int tot = block_exclusive_scan(s, &excl);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// One CTA scans the tile sums in place (exclusive), in chunks of SCAN_THREADS.
+__global__ void __launch_bounds__(SCAN_THREADS) scan_sums(int *sums, int64_t nt) {
+    __shared__ int carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < nt; b += SCAN_THREADS) {
+        const int64_t idx = b + threadIdx.x;
+        const int v = idx < nt ? sums[idx] : 0;
+        int excl;
+        const int tot = block_exclusive_scan(v, &excl);
+        const int carry = carry_s;
+        if (idx < nt) sums[idx] = carry + excl;
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s = carry + tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_tiles(const int *__restrict__ in, int64_t n,
+                                                           const int *__restrict__ sums, int *__restrict__ out) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int s = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        v[q] = base + q < n ? in[base + q] : 0;
+        s += v[q];
+    }
+    int excl;
+    const int tot = block_exclusive_scan(s, &excl);
+    int run = sums[blockIdx.x] + excl;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        if (base + q < n) out[base + q] = run;
+        run += v[q];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = sums[blockIdx.x] + tot;
+}
+
+}  // namespace
+
+int64_t ptp_scan_tmp_ints(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 1; }
+
+ptp_status ptp_exclusive_scan(const int *in, int *out, int64_t n, int *tmp, cudaStream_t s) {
+    if (n <= 0) {
+        PTP_TRY(cudaMemsetAsync(out, 0, sizeof(int), s));
+        return PTP_OK;
+    }
+    const int64_t nt = (n + SCAN_TILE - 1) / SCAN_TILE;
+    scan_tile_sums<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, tmp);
+    scan_sums<<<1, SCAN_THREADS, 0, s>>>(tmp, nt);
+    scan_tiles<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, tmp, out);
+    PTP_TRY(cudaGetLastError());
+    return PTP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mesh kernels
+// ---------------------------------------------------------------------------
+
+namespace {
+
+__global__ void validate_faces(const int *__restrict__ F, int64_t nf, int64_t n, int *__restrict__ err) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+        const int a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
+        if (a < 0 || a >= n || b < 0 || b >= n || c < 0 || c >= n) atomicOr(err, 1);
+        else if (a == b || b == c || a == c) atomicOr(err, 2);
+    }
+}
+
+__global__ void count_corners(const int *__restrict__ F, int64_t nc, int *__restrict__ deg) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&deg[F[c]], 1);
+}
+
+__global__ void fill_corners(const int *__restrict__ F, int64_t nf, const int *__restrict__ row,
+                             int *__restrict__ cursor, int2 *__restrict__ pairs) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+        const int t[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int v = t[s];
+            const int slot = row[v] + atomicAdd(&cursor[v], 1);
+            pairs[slot] = make_int2(t[(s + 1) % 3], t[(s + 2) % 3]);
+        }
+    }
+}
+
+// float32 xyz -> float4; also a per-block bounding box into bb[6] using the
+// order-preserving integer image of each float.
+__device__ __forceinline__ int float_key(float f) {
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+
+__global__ void pack_positions(const float *__restrict__ xyz, int64_t n, float4 *__restrict__ pos, int *__restrict__ bb) {
+    float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const float x = xyz[3 * v], y = xyz[3 * v + 1], z = xyz[3 * v + 2];
+        pos[v] = make_float4(x, y, z, 0.0f);
+        mn[0] = fminf(mn[0], x); mn[1] = fminf(mn[1], y); mn[2] = fminf(mn[2], z);
+        mx[0] = fmaxf(mx[0], x); mx[1] = fmaxf(mx[1], y); mx[2] = fmaxf(mx[2], z);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[q] = fminf(mn[q], __shfl_xor_sync(0xffffffffu, mn[q], o));
+            mx[q] = fmaxf(mx[q], __shfl_xor_sync(0xffffffffu, mx[q], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            atomicMin(&bb[q], float_key(mn[q]));
+            atomicMax(&bb[3 + q], float_key(mx[q]));
+        }
+    }
+}
+
+__global__ void init_bbox(int *bb) {
+    if (threadIdx.x < 3) bb[threadIdx.x] = 0x7fffffff;
+    else if (threadIdx.x < 6) bb[threadIdx.x] = (int)0x80000000;
+}
+
+unsigned grid_for(int64_t work, int threads, int device) {
+    int64_t b = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)ptp_num_sms(device) * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+extern "C" ptp_status ptp_mesh_create(const float *xyz, int64_t n_verts, const int32_t *faces, int64_t n_faces,
+                                      int ptr_kind, void *stream, ptp_mesh **out) {
+    if (!out) return PTP_ERR_ARG;
+    *out = nullptr;
+    if (!xyz || !faces || n_verts < 3 || n_faces < 1 || (ptr_kind != PTP_HOST && ptr_kind != PTP_DEVICE))
+        return PTP_ERR_ARG;
+    if (3 * n_faces > 2147483647LL || n_verts > 2147483646LL) return PTP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    PTP_TRY(cudaGetDevice(&dev));
+
+    ptp_mesh *m = (ptp_mesh *)calloc(1, sizeof(ptp_mesh));
+    if (!m) return PTP_ERR_NOMEM;
+    m->device = dev;
+    m->stream = s;
+    m->n = n_verts;
+    m->nf = n_faces;
+    const int64_t nc = 3 * n_faces;
+
+    float *xyz_d = nullptr;
+    int *F_d = nullptr, *deg = nullptr, *tmp = nullptr, *err = nullptr;
+    ptp_status st = PTP_OK;
+    int herr[8] = {0};
+    cudaError_t ce = cudaSuccess;
+#define MESH_TRY(call)                                   \
+    do {                                                 \
+        ce = (call);                                     \
+        if (ce != cudaSuccess) {                         \
+            st = ptp_internal_cuda_status(ce);           \
+            goto fail;                                   \
+        }                                                \
+    } while (0)
+
+    MESH_TRY(cudaMallocAsync((void **)&m->pos, sizeof(float4) * n_verts, s));
+    MESH_TRY(cudaMallocAsync((void **)&m->row, sizeof(int) * (n_verts + 1), s));
+    MESH_TRY(cudaMallocAsync((void **)&m->pairs, sizeof(int2) * nc, s));
+    MESH_TRY(cudaMallocAsync((void **)&deg, sizeof(int) * (2 * n_verts + 8), s));
+    MESH_TRY(cudaMallocAsync((void **)&tmp, sizeof(int) * ptp_scan_tmp_ints(n_verts), s));
+    err = deg + 2 * n_verts;  // [0] face errors, [2..7] bbox keys
+    if (ptr_kind == PTP_HOST) {
+        MESH_TRY(cudaMallocAsync((void **)&xyz_d, sizeof(float) * 3 * n_verts, s));
+        MESH_TRY(cudaMallocAsync((void **)&F_d, sizeof(int) * nc, s));
+        MESH_TRY(cudaMemcpyAsync(xyz_d, xyz, sizeof(float) * 3 * n_verts, cudaMemcpyHostToDevice, s));
+        MESH_TRY(cudaMemcpyAsync(F_d, faces, sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+    } else {
+        xyz_d = (float *)xyz;
+        F_d = (int *)faces;
+    }
+    MESH_TRY(cudaMemsetAsync(deg, 0, sizeof(int) * (2 * n_verts + 8), s));
+    init_bbox<<<1, 32, 0, s>>>(err + 2);
+    validate_faces<<<grid_for(n_faces, 256, dev), 256, 0, s>>>(F_d, n_faces, n_verts, err);
+    pack_positions<<<grid_for(n_verts, 256, dev), 256, 0, s>>>(xyz_d, n_verts, m->pos, err + 2);
+    MESH_TRY(cudaGetLastError());
+    MESH_TRY(cudaMemcpyAsync(herr, err, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
+    MESH_TRY(cudaStreamSynchronize(s));
+    if (herr[0] & 1) { st = PTP_ERR_INDEX; goto fail; }
+    if (herr[0] & 2) { st = PTP_ERR_DEGENERATE_FACE; goto fail; }
+    {
+        double d2 = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            auto kf = [](int k) { unsigned u = (unsigned)(k >= 0 ? k : k ^ 0x7fffffff); float f; memcpy(&f, &u, 4); return f; };
+            const double e = (double)kf(herr[5 + q]) - (double)kf(herr[2 + q]);
+            d2 += e * e;
+        }
+        m->diameter = sqrt(d2);
+    }
+    count_corners<<<grid_for(nc, 256, dev), 256, 0, s>>>(F_d, nc, deg);
+    MESH_TRY(cudaGetLastError());
+    st = ptp_exclusive_scan(deg, m->row, n_verts, tmp, s);
+    if (st != PTP_OK) goto fail;
+    MESH_TRY(cudaMemsetAsync(deg + n_verts, 0, sizeof(int) * n_verts, s));
+    fill_corners<<<grid_for(n_faces, 256, dev), 256, 0, s>>>(F_d, n_faces, m->row, deg + n_verts, m->pairs);
+    MESH_TRY(cudaGetLastError());
+    if (ptr_kind == PTP_HOST) {
+        cudaFreeAsync(xyz_d, s);
+        cudaFreeAsync(F_d, s);
+    }
+    cudaFreeAsync(deg, s);
+    cudaFreeAsync(tmp, s);
+    *out = m;
+    return PTP_OK;
+
+fail:
+    if (ptr_kind == PTP_HOST) {
+        if (xyz_d) cudaFreeAsync(xyz_d, s);
+        if (F_d) cudaFreeAsync(F_d, s);
+    }
+    if (deg) cudaFreeAsync(deg, s);
+    if (tmp) cudaFreeAsync(tmp, s);
+    if (m->pos) cudaFreeAsync(m->pos, s);
+    if (m->row) cudaFreeAsync(m->row, s);
+    if (m->pairs) cudaFreeAsync(m->pairs, s);
+    cudaStreamSynchronize(s);
+    free(m);
+    return st;
+#undef MESH_TRY
+}
+
+extern "C" ptp_status ptp_mesh_info(const ptp_mesh *m, int64_t *n_verts, int64_t *n_faces, double *diameter) {
+    if (!m) return PTP_ERR_ARG;
+    if (n_verts) *n_verts = m->n;
+    if (n_faces) *n_faces = m->nf;
+    if (diameter) *diameter = m->diameter;
+    return PTP_OK;
+}
+
+extern "C" ptp_status ptp_mesh_destroy(ptp_mesh *m) {
+    if (!m) return PTP_ERR_ARG;
+    cudaFreeAsync(m->pos, m->stream);
+    cudaFreeAsync(m->row, m->stream);
+    cudaFreeAsync(m->pairs, m->stream);
+    const cudaError_t e = cudaStreamSynchronize(m->stream);
+    free(m);
+    return e == cudaSuccess ? PTP_OK : ptp_internal_cuda_status(e);
+}
