@@ -71,6 +71,9 @@ typedef struct ptp_params {
     void *trace;       /* optional DEVICE buffer of trace_cap ptp_trace_rec, one per
                           iteration, or NULL                                       */
     int64_t trace_cap;
+    void *ev_begin;    /* optional cudaEvent_t recorded on `stream` right before the
+                          window kernel, or NULL                                   */
+    void *ev_end;      /* optional cudaEvent_t recorded right after it, or NULL     */
 } ptp_params;
 
 /* One record per PTP iteration k (written only when params.trace is set). */
@@ -98,8 +101,12 @@ typedef struct ptp_stats {
 const char *ptp_status_str(ptp_status s);
 
 /* Defaults: eps = 1e-3 and eps_abs = 0 (Sec. 3.2, the paper's setting),
- * max_iter = 0 (auto), block = grid = 0 (auto), no trace. */
+ * max_iter = 0 (auto), block = grid = 0 (auto), no trace, no events. */
 ptp_status ptp_params_default(ptp_params *p);
+
+/* Number of CUDA kernel launches this library has issued in this process
+ * (all devices, all entry points).  Never blocks. */
+int64_t ptp_kernel_launches(void);
 
 /*
  * Build the device mesh (Sec. 3.1, T = (V, E, F); Sec. 3.3 stores it as a

@@ -32,11 +32,12 @@ ERR_DEGENERATE_FACE = -3
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, no fast-math, no target flags)."""
+    """Compile the oracle with gcc (-O2, no fast-math, no FMA contraction, no
+    target flags, so x86 and Arm builds round identically)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 

@@ -42,7 +42,7 @@ class PTPError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("eps_abs", ctypes.c_double), ("max_iter", ctypes.c_int64),
                 ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("trace", ctypes.c_void_p),
-                ("trace_cap", ctypes.c_int64)]
+                ("trace_cap", ctypes.c_int64), ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -79,6 +79,7 @@ def load(path: str | None = None):
         sig = {
             "ptp_status_str": (ctypes.c_char_p, [st]),
             "ptp_params_default": (st, [P]),
+            "ptp_kernel_launches": (i64, []),
             "ptp_mesh_create": (st, [P, i64, P, i64, ctypes.c_int, P, P]),
             "ptp_mesh_info": (st, [P, P, P, P]),
             "ptp_mesh_destroy": (st, [P]),
@@ -190,6 +191,10 @@ def ptp_params_default(**overrides) -> Params:
     for k, v in overrides.items():
         setattr(p, k, v)
     return p
+
+
+def ptp_kernel_launches() -> int:
+    return int(load().ptp_kernel_launches())
 
 
 def ptp_mesh_create(xyz, faces, stream=None) -> Mesh:

@@ -473,6 +473,7 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
             if (ce != cudaSuccess) break;
         }
         init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->off, (int)n, dbuf, dbuf + n, ibuf, ibuf + n);
+        ptp_count_launches(1);
         ce = cudaGetLastError();
         if (ce != cudaSuccess) break;
 
@@ -502,9 +503,19 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
         a.eps_abs = params->eps_abs;
         a.max_iter = params->max_iter;
         void *args[] = {(void *)&a};
+        if (params->ev_begin) {
+            ce = cudaEventRecord((cudaEvent_t)params->ev_begin, s);
+            if (ce != cudaSuccess) break;
+        }
         ce = cudaLaunchCooperativeKernel((const void *)ptp_window, dim3(grid), dim3(DIST_THREADS), args, 0, s);
         if (ce != cudaSuccess) break;
+        ptp_count_launches(1);
+        if (params->ev_end) {
+            ce = cudaEventRecord((cudaEvent_t)params->ev_end, s);
+            if (ce != cudaSuccess) break;
+        }
         scatter_out<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, dbuf, dbuf + n, t->ctrl, d_out);
+        ptp_count_launches(1);
         ce = cudaGetLastError();
     } while (0);
     cudaFreeAsync(dbuf, s);

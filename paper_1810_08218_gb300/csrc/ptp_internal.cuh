@@ -85,6 +85,9 @@ struct ptp_toplesets_s {
 
 int ptp_num_sms(int device);
 
+// Counts kernel launches issued by the library (ptp_kernel_launches).
+void ptp_count_launches(int n);
+
 // Exclusive scan of n int32 values: out[0..n] with out[n] = total.
 // `tmp` must hold ptp_scan_tmp_ints(n) ints.
 int64_t ptp_scan_tmp_ints(int64_t n);

@@ -38,8 +38,16 @@ extern "C" ptp_status ptp_params_default(ptp_params *p) {
     p->grid = 0;
     p->trace = nullptr;
     p->trace_cap = 0;
+    p->ev_begin = nullptr;
+    p->ev_end = nullptr;
     return PTP_OK;
 }
+
+static unsigned long long g_launches = 0;
+
+void ptp_count_launches(int n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+
+extern "C" int64_t ptp_kernel_launches(void) { return (int64_t)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 int ptp_num_sms(int device) {
     int v = 0;
@@ -151,6 +159,7 @@ ptp_status ptp_exclusive_scan(const int *in, int *out, int64_t n, int *tmp, cuda
     scan_tile_sums<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, tmp);
     scan_sums<<<1, SCAN_THREADS, 0, s>>>(tmp, nt);
     scan_tiles<<<(unsigned)nt, SCAN_THREADS, 0, s>>>(in, n, tmp, out);
+    ptp_count_launches(3);
     PTP_TRY(cudaGetLastError());
     return PTP_OK;
 }
@@ -286,6 +295,7 @@ extern "C" ptp_status ptp_mesh_create(const float *xyz, int64_t n_verts, const i
     init_bbox<<<1, 32, 0, s>>>(err + 2);
     validate_faces<<<grid_for(n_faces, 256, dev), 256, 0, s>>>(F_d, n_faces, n_verts, err);
     pack_positions<<<grid_for(n_verts, 256, dev), 256, 0, s>>>(xyz_d, n_verts, m->pos, err + 2);
+    ptp_count_launches(3);
     MESH_TRY(cudaGetLastError());
     MESH_TRY(cudaMemcpyAsync(herr, err, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
     MESH_TRY(cudaStreamSynchronize(s));
@@ -301,11 +311,13 @@ extern "C" ptp_status ptp_mesh_create(const float *xyz, int64_t n_verts, const i
         m->diameter = sqrt(d2);
     }
     count_corners<<<grid_for(nc, 256, dev), 256, 0, s>>>(F_d, nc, deg);
+    ptp_count_launches(1);
     MESH_TRY(cudaGetLastError());
     st = ptp_exclusive_scan(deg, m->row, n_verts, tmp, s);
     if (st != PTP_OK) goto fail;
     MESH_TRY(cudaMemsetAsync(deg + n_verts, 0, sizeof(int) * n_verts, s));
     fill_corners<<<grid_for(n_faces, 256, dev), 256, 0, s>>>(F_d, n_faces, m->row, deg + n_verts, m->pairs);
+    ptp_count_launches(1);
     MESH_TRY(cudaGetLastError());
     if (ptr_kind == PTP_HOST) {
         cudaFreeAsync(xyz_d, s);

@@ -321,6 +321,7 @@ extern "C" ptp_status ptp_toplesets(ptp_mesh *mesh, const int32_t *sources, int3
         TOPS_TRY(cudaMemsetAsync(bfs_cnt, 0, sizeof(int) * 16, s));
         TOPS_TRY(cudaMemsetAsync(t->ctrl, 0, sizeof(ptp_ctrl), s));
         bfs_seed<<<blocks_for(m, 256, dev), 256, 0, s>>>(src_d, m, t->level, t->perm, t->info, bfs_cnt);
+        ptp_count_launches(1);
         TOPS_TRY(cudaGetLastError());
 
         // persistent BFS: every CTA co-resident
@@ -336,15 +337,18 @@ extern "C" ptp_status ptp_toplesets(ptp_mesh *mesh, const int32_t *sources, int3
             void *args[] = {(void *)&row_c, (void *)&pairs_c, (void *)&t->level, (void *)&t->perm, (void *)&t->off,
                             (void *)&t->info, (void *)&bfs_bar, (void *)&tail, (void *)&abort_flag};
             TOPS_TRY(cudaLaunchCooperativeKernel((const void *)bfs_levels, dim3(nblk), dim3(BFS_THREADS), args, 0, s));
+            ptp_count_launches(1);
         }
         append_unreached<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->level, (int)n, t->perm, t->info, bfs_cnt + 4);
         invert_perm<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, t->iperm, mesh->pos, t->pos, mesh->row, ndeg);
+        ptp_count_launches(2);
         TOPS_TRY(cudaGetLastError());
         st = ptp_exclusive_scan(ndeg, t->row, n, tmp, s);
         if (st != PTP_OK) goto fail;
         renumber_corners<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, t->iperm, (int)n, mesh->row, mesh->pairs, t->row,
                                                                 t->pairs);
         build_rings<<<blocks_for(n, 128, dev), 128, 0, s>>>((int)n, t->row, t->pairs, t->ring, t->meta);
+        ptp_count_launches(2);
         TOPS_TRY(cudaGetLastError());
         cudaFreeAsync(work, s);
         cudaFreeAsync(src_d, s);
