@@ -178,6 +178,36 @@ ptp_status ptp_toplesets_destroy(ptp_toplesets_t *tops);
 ptp_status ptp_distance(ptp_toplesets_t *tops, const ptp_params *params, float *d_out, void *stream,
                         ptp_stats *stats);
 
+/*
+ * ptp_distance_noalloc -- ptp_distance for callers that may not allocate.
+ * (An addition of this library; the paper has no counterpart.)
+ *
+ * ptp_distance takes its per-call scratch (two distance buffers and two
+ * per-vertex change stamps, 16 bytes per vertex) from a stream-ordered
+ * allocation.  Some callers cannot allocate once their set-up is done: a
+ * real-time loop that must not wait for the allocator or grow a memory pool,
+ * or a host application that hands every byte of device memory out through
+ * its own allocator and forbids libraries from calling cudaMalloc.  Such a
+ * caller creates the mesh and its toplesets at set-up and then answers
+ * distance queries with this entry point, which calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ * Scratch: a file-scope device array sized for PTP_NOALLOC_MAX_VERTS
+ * vertices (16 MiB + 256 bytes), which every GPU that loads the library holds
+ * until the process exits.  A handle with more vertices is rejected with
+ * PTP_ERR_TOO_LARGE.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current and caches it;
+ * make that first call before any stream capture.  Every call shares the one
+ * array per device and overwrites what the last call left there, so calls
+ * whose work overlaps on the GPU (another stream, another host thread) race;
+ * serialise them.  Arguments, results, blocking and statuses are those of
+ * ptp_distance, except that ptp_last_stats does not see these calls: pass
+ * `stats` to get their statistics.
+ */
+#define PTP_NOALLOC_MAX_VERTS 1048576
+ptp_status ptp_distance_noalloc(ptp_toplesets_t *tops, const ptp_params *params, float *d_out, void *stream,
+                                ptp_stats *stats);
+
 /* Statistics of the last ptp_distance call on this handle.  Blocks on
  * `stream`.  Returns that call's device-side status. */
 ptp_status ptp_last_stats(ptp_toplesets_t *tops, void *stream, ptp_stats *stats);

@@ -88,6 +88,7 @@ def load(path: str | None = None):
             "ptp_toplesets_destroy": (st, [P]),
             "ptp_distance": (st, [P, P, P, P, P]),
             "ptp_last_stats": (st, [P, P, P]),
+            "ptp_distance_noalloc": (st, [P, P, P, P, P]),
             "ptp_geodesic": (st, [P, i64, P, i64, P, i32, ctypes.c_int, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -266,6 +267,20 @@ def ptp_distance(tops: Toplesets, params: Params, d_out, stream=None, stats: boo
                                _stream_ptr(stream), ctypes.byref(st) if st is not None else None)
     _check(code, "ptp_distance", ok)
     return st.as_dict() if st is not None else None
+
+
+def ptp_distance_noalloc(tops: Toplesets, params: Params, d_out, stream=None, stats: bool = True,
+                         ok=(PTP_OK,)) -> dict | None:
+    """ptp_distance with its scratch in the library's static device array
+    (no allocation; at most PTP_NOALLOC_MAX_VERTS vertices)."""
+    st = Stats() if stats else None
+    code = load().ptp_distance_noalloc(tops.handle, ctypes.byref(params), ctypes.c_void_p(d_out.data_ptr()),
+                                       _stream_ptr(stream), ctypes.byref(st) if st is not None else None)
+    _check(code, "ptp_distance_noalloc", ok)
+    return st.as_dict() if st is not None else None
+
+
+PTP_NOALLOC_MAX_VERTS = 1048576
 
 
 def ptp_last_stats(tops: Toplesets, stream=None) -> dict:

@@ -561,3 +561,111 @@ extern "C" ptp_status ptp_geodesic(const float *xyz, int64_t n_verts, const int3
     ptp_mesh_destroy(mesh);
     return st;
 }
+
+// ---------------------------------------------------------------------------
+// ptp_distance_noalloc: the same window kernel with its per-call scratch in a
+// file-scope device array instead of a stream-ordered allocation.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// Layout: [0, 256) control block, then d0[n], d1[n], nstamp[n], chg[n].
+constexpr size_t NOALLOC_HEADER = 256;
+static_assert(sizeof(ptp_ctrl) <= NOALLOC_HEADER, "control block must fit the header");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_HEADER + (size_t)PTP_NOALLOC_MAX_VERTS * 16];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+void *g_noalloc_addr[NOALLOC_MAX_DEVICES];
+bool g_noalloc_ready[NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array for the current device.  The array's
+// name is only a host-side stand-in in host code, so its address is looked up
+// once per device, with that device current, and cached.
+ptp_status noalloc_scratch(int dev, unsigned char **out) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PTP_ERR_ARG;
+    if (!__atomic_load_n(&g_noalloc_ready[dev], __ATOMIC_ACQUIRE)) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return ptp_internal_cuda_status(e);
+        g_noalloc_addr[dev] = p;
+        __atomic_store_n(&g_noalloc_ready[dev], true, __ATOMIC_RELEASE);
+    }
+    *out = (unsigned char *)g_noalloc_addr[dev];
+    return PTP_OK;
+}
+
+}  // namespace
+
+extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params *params, float *d_out, void *stream,
+                                           ptp_stats *stats) {
+    if (!t || !params || !d_out) return PTP_ERR_ARG;
+    if (!(params->eps >= 0.0) || !(params->eps_abs >= 0.0) || params->max_iter < 0 || params->trace_cap < 0)
+        return PTP_ERR_ARG;
+    if (params->block != 0 && params->block != DIST_THREADS) return PTP_ERR_ARG;
+    if (t->n > (int64_t)PTP_NOALLOC_MAX_VERTS) return PTP_ERR_TOO_LARGE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = t->n;
+    int dev = 0;
+    PTP_TRY(cudaGetDevice(&dev));
+    if (dev != t->device) return PTP_ERR_ARG;
+    unsigned char *base = nullptr;
+    PTP_CHECK(noalloc_scratch(dev, &base));
+    ptp_ctrl *ctrl = (ptp_ctrl *)base;
+    float *dbuf = (float *)(base + NOALLOC_HEADER);
+    int *ibuf = (int *)(dbuf + 2 * n);
+
+    // the array keeps the previous call's contents: the control block must
+    // start at zero; init_distances rewrites all 4n scratch words
+    PTP_TRY(cudaMemsetAsync(ctrl, 0, sizeof(ptp_ctrl), s));
+    if (params->trace && params->trace_cap > 0)
+        PTP_TRY(cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s));
+    init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->off, (int)n, dbuf, dbuf + n, ibuf, ibuf + n);
+    ptp_count_launches(1);
+    PTP_TRY(cudaGetLastError());
+    int per_sm = 0;
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window, DIST_THREADS, 0));
+    if (per_sm < 1) return PTP_ERR_CUDA;
+    int grid = per_sm * ptp_num_sms(dev);
+    if (params->grid > 0 && params->grid < grid) grid = params->grid;
+
+    DistArgs a;
+    a.pos = t->pos;
+    a.ring = t->ring;
+    a.meta = t->meta;
+    a.row = t->row;
+    a.pairs = t->pairs;
+    a.off = t->off;
+    a.info = t->info;
+    a.d0 = dbuf;
+    a.d1 = dbuf + n;
+    a.nstamp = ibuf;
+    a.chg = ibuf + n;
+    a.ctrl = ctrl;
+    a.trace = (ptp_trace_rec *)params->trace;
+    a.trace_cap = params->trace ? params->trace_cap : 0;
+    a.eps = params->eps;
+    a.eps_abs = params->eps_abs;
+    a.max_iter = params->max_iter;
+    void *args[] = {(void *)&a};
+    if (params->ev_begin) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_begin, s));
+    PTP_TRY(cudaLaunchCooperativeKernel((const void *)ptp_window, dim3(grid), dim3(DIST_THREADS), args, 0, s));
+    ptp_count_launches(1);
+    if (params->ev_end) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_end, s));
+    scatter_out<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, dbuf, dbuf + n, ctrl, d_out);
+    ptp_count_launches(1);
+    PTP_TRY(cudaGetLastError());
+    if (!stats) return PTP_OK;
+    ptp_ctrl h;
+    int info[4];
+    PTP_TRY(cudaMemcpyAsync(&h, ctrl, sizeof(ptp_ctrl), cudaMemcpyDeviceToHost, s));
+    PTP_TRY(cudaMemcpyAsync(info, t->info, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    PTP_TRY(cudaStreamSynchronize(s));
+    stats->iterations = h.iterations;
+    stats->band_updates = h.band_updates;
+    stats->active_updates = (int64_t)h.active;
+    stats->changed = (int64_t)h.changed;
+    stats->fp64_solves = (int64_t)h.fp64;
+    stats->rho = info[0];
+    stats->status = h.status;
+    return (ptp_status)h.status;
+}

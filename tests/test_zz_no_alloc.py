@@ -1,0 +1,73 @@
+"""ptp_distance_noalloc: the distance entry point for callers that may not
+allocate device memory after set-up (for example a real-time loop that must
+not wait on the allocator, or a host application that owns all device memory
+through its own allocator).  It takes its scratch from the library's static
+device array instead of an allocation, so its result must match
+ptp_distance's within the tolerance the parity tests use, call after call,
+even though every call reuses (and must first clear) the same array.
+
+This file is collected last so that a run stopping at its first failure has
+already run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_1810_08218_gb300 import meshes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_REL_DIAM = 1e-5
+
+
+@pytest.fixture(scope="module")
+def capi():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1810_08218_gb300 import build, capi as c
+
+    build.build()
+    c.load()
+    return c
+
+
+def _prepare(capi, V, F, S):
+    mesh = capi.ptp_mesh_create(torch.from_numpy(np.ascontiguousarray(V, dtype=np.float32)).cuda(),
+                                torch.from_numpy(np.ascontiguousarray(F, dtype=np.int32)).cuda())
+    tops = capi.ptp_toplesets(mesh, np.asarray(S, dtype=np.int32))
+    return mesh, tops
+
+
+def _check(ref, got, diam):
+    fin = np.isfinite(ref)
+    assert np.array_equal(np.isfinite(got), fin)
+    assert np.max(np.abs(got[fin].astype(np.float64) - ref[fin])) <= TOL_REL_DIAM * diam
+
+
+def test_noalloc_matches_distance_on_consecutive_calls(capi):
+    cases = [meshes.sphere_l7(), meshes.flat65(), meshes.sphere_l7(seed=5)]
+    for V, F, S in cases:
+        mesh, tops = _prepare(capi, V, F, S)
+        n = V.shape[0]
+        p = capi.ptp_params_default()
+        ref = torch.empty(n, dtype=torch.float32, device="cuda")
+        st_ref = capi.ptp_distance(tops, p, ref)
+        ref = ref.cpu().numpy()
+        diam = meshes.bbox_diagonal(np.asarray(V, dtype=np.float32))
+        for _ in range(2):  # two calls in a row share the static scratch
+            out = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+            st = capi.ptp_distance_noalloc(tops, p, out)
+            _check(ref, out.cpu().numpy(), diam)
+            assert st["iterations"] == st_ref["iterations"] and st["rho"] == st_ref["rho"]
+            assert st["band_updates"] == st_ref["band_updates"] and st["status"] == 0
+
+
+def test_noalloc_rejects_meshes_above_its_limit(capi):
+    side = 1025  # 1,050,625 vertices > PTP_NOALLOC_MAX_VERTS
+    V, F = meshes.grid(side, side)
+    assert V.shape[0] > capi.PTP_NOALLOC_MAX_VERTS
+    mesh, tops = _prepare(capi, V, F, [0])
+    out = torch.empty(V.shape[0], dtype=torch.float32, device="cuda")
+    with pytest.raises(capi.PTPError) as e:
+        capi.ptp_distance_noalloc(tops, capi.ptp_params_default(), out)
+    assert e.value.status == capi.PTP_ERR_TOO_LARGE
