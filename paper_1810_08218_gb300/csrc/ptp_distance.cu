@@ -19,7 +19,8 @@
 // the discriminant written as det * (L - |d2-d1|) (L + |d2-d1|), L = |x2-x1|,
 // so neither the magnitude of d nor the front's alignment with an edge
 // cancels digits.  Near-degenerate triangles (some angle with squared sine
-// below 1e-6) and the rare residual cancellation are solved in FP64.  The
+// below 1e-6) are solved in FP64; when the discriminant itself is too small
+// for FP32 the triangle is provably non-causal (see tri_update).  The
 // relative-change test of Eq. lower_band is evaluated in FP64.
 #include <math.h>
 #include <stdlib.h>
@@ -29,11 +30,17 @@
 namespace {
 
 constexpr int DIST_THREADS = 512;
+constexpr int ROUND_CHUNKS = 8;                                 // chunks per warp per round
+constexpr int P1_BATCH = 4;                                     // chunks whose state loads overlap
+constexpr int QUEUE_CAP = ROUND_CHUNKS * DIST_THREADS;         // queue entries per CTA
 #define INF __int_as_float(0x7f800000)
 
 struct DistArgs {
+    int n;
     const float4 *__restrict__ pos;
     const int4 *__restrict__ ring;
+    const float4 *__restrict__ tgeom;
+    const float4 *__restrict__ elen;
     const int *__restrict__ meta;
     const int *__restrict__ row;
     const int2 *__restrict__ pairs;
@@ -111,10 +118,13 @@ __device__ __forceinline__ float tri_update(float3 e1, float3 e2, float d1, floa
     }
     if (!(ad < L)) return fb;
     const float disc = (L - ad) * (L + ad);
-    if (disc < 0x1p-20f * A) {
-        ++nfp64;
-        return tri_solve_fp64(e1, e2, d1, d2, fb);
-    }
+    // The planar solution is causal only if
+    //   disc > A det / (max((a-b)^2, (c-b)^2) + det),
+    // and since (a-b)^2, (c-b)^2 <= big, a triangle that passed the test
+    // above (det >= 1e-6 big) needs disc > ~1e-6 A.  A computed disc below
+    // 2^-22 A (where its own rounding error becomes large) is therefore
+    // certainly non-causal: the edge fallback is exact here, no FP64 needed.
+    if (disc < 0x1p-22f * A) return fb;
     const float amb = -dot3(e1, e12);  // a - b
     const float cmb = dot3(e2, e12);   // c - b
     const float q = __fdividef(fmaf(delta, amb, fsqrt(det * disc)), A);
@@ -124,37 +134,58 @@ __device__ __forceinline__ float tri_update(float3 e1, float3 e2, float d1, floa
 
 __device__ __forceinline__ float3 xyz(float4 p) { return make_float3(p.x, p.y, p.z); }
 
+// Update step (Sec. 2.2) for vertex u from ring triangle (u, x1, x2) with
+// the triangle's precomputed geometry g = (b, L, alpha, beta) and edge
+// lengths l1 = |x1 - x_u|, l2 = |x2 - x_u|: q = delta * alpha + beta *
+// sqrt(disc) is the planar solution shifted by d1, kept when both
+// monotonicity conditions hold, else min(d1 + l1, d2 + l2).
+__device__ __forceinline__ float tri_update_geom(float4 g, float d1, float d2, float l1, float l2) {
+    const float fb = fminf(d1 + l1, d2 + l2);
+    if (!(fmaxf(d1, d2) < INF)) return fb;  // at most one finite neighbour: edge only
+    const float delta = d2 - d1;
+    const float ad = fabsf(delta);
+    const float L = g.y;
+    if (!(ad < L)) return fb;
+    const float disc = (L - ad) * (L + ad);
+    if (disc < 0x1p-22f * (L * L)) return fb;  // provably non-causal, see tri_update
+    const float q = fmaf(delta, g.z, g.w * fsqrt(disc));
+    const float b = g.x, a1 = l1 * l1, c = l2 * l2;
+    const bool causal = (fmaf(c - b, q, b * delta) > 0.0f) && (fmaf(a1 - b, q, -a1 * delta) > 0.0f);
+    return causal ? fminf(d1 + q, fb) : fb;
+}
+
+// Near-degenerate ring triangle: solve from the positions in FP64.
+__device__ __noinline__ float tri_update_degenerate(const DistArgs &a, int u, int id1, int id2, float d1, float d2,
+                                                    float l1, float l2) {
+    const float fb = fminf(d1 + l1, d2 + l2);
+    if (!(fmaxf(d1, d2) < INF)) return fb;
+    const float3 x0 = xyz(__ldg(a.pos + u));
+    return tri_solve_fp64(sub3(xyz(__ldg(a.pos + id1)), x0), sub3(xyz(__ldg(a.pos + id2)), x0), d1, d2, fb);
+}
+
 // New value of a ring-slot vertex: min of the old value and the update over
-// its fan.  All neighbour loads are issued first (one dependent round trip);
-// the edge lengths roll along the fan.  Triangles whose two neighbours are
-// both no closer than the current best are skipped: the update never
-// returns less than min(d1, d2).
-__device__ __forceinline__ float update_ring(const DistArgs &a, const int ids[PTP_RING], float3 x0, int m, float best,
-                                             const float *__restrict__ dp, unsigned &nfp64) {
-    float3 e[PTP_RING];
+// its fan.  The geometry was loaded with the ring (one round trip); here
+// only the neighbours' distances are gathered (the second).  Triangles whose
+// two neighbours are both no closer than the current best are skipped: the
+// update never returns less than min(d1, d2).
+__device__ __forceinline__ float update_ring(const DistArgs &a, int u, const int ids[PTP_RING], const float el[PTP_RING],
+                                             const float4 g[PTP_TRI], int m, float best, const float *__restrict__ dp,
+                                             unsigned &nfp64) {
     float dn[PTP_RING];
 #pragma unroll
-    for (int t = 0; t < PTP_RING; ++t) {
-        if (t < m) {
-            e[t] = sub3(xyz(__ldg(a.pos + ids[t])), x0);
-            dn[t] = __ldcg(dp + ids[t]);
-        } else {
-            e[t] = make_float3(0.0f, 0.0f, 0.0f);
-            dn[t] = INF;
-        }
-    }
-    float a_prev = dot3(e[0], e[0]);
-    float l_prev = fsqrt(a_prev);
+    for (int t = 0; t < PTP_RING; ++t) dn[t] = t < m ? __ldcg(dp + ids[t]) : INF;
 #pragma unroll
-    for (int t = 0; t < PTP_RING - 1; ++t) {
-        const float a_next = dot3(e[t + 1], e[t + 1]);
-        const float l_next = fsqrt(a_next);
+    for (int t = 0; t < PTP_TRI; ++t) {
         if (t < m - 1 && fminf(dn[t], dn[t + 1]) < best) {
-            const float c = tri_update(e[t], e[t + 1], dn[t], dn[t + 1], a_prev, l_prev, a_next, l_next, nfp64);
+            float c;
+            if (g[t].w >= 0.0f) {
+                c = tri_update_geom(g[t], dn[t], dn[t + 1], el[t], el[t + 1]);
+            } else {
+                ++nfp64;
+                c = tri_update_degenerate(a, u, ids[t], ids[t + 1], dn[t], dn[t + 1], el[t], el[t + 1]);
+            }
             best = fminf(best, c);
         }
-        a_prev = a_next;
-        l_prev = l_next;
     }
     return best;
 }
@@ -213,19 +244,23 @@ struct Band {
     int hi;       // off[j + 1]
 };
 
-// The persistent window kernel.  Work is dealt out in chunks of 32
-// consecutive renumbered vertices (coalesced), chunk c to warp c mod W with
-// the warps numbered across CTAs first, so even a narrow band spreads over
-// all SMs.  Everything indexed by the vertex itself is loaded in one round
-// trip before deciding whether to recompute it, and the next iteration's
-// band bounds are fetched before the barrier, so after the barrier only the
-// neighbours' distances are on the critical path.
+// The persistent window kernel.  Each iteration walks the band in chunks of
+// 32 consecutive renumbered vertices (coalesced), chunk c to warp c mod W
+// with the warps numbered across CTAs first, so even a narrow band spreads
+// over all SMs.  Pass 1 reads each vertex's own distance and change stamps
+// and queues, in shared memory, the vertices some neighbour of which
+// changed in the previous iteration; pass 2 recomputes the queued vertices
+// with every lane busy.  Long bands are handled in rounds that fit the
+// queue.  The next iteration's band bounds are fetched before the barrier,
+// so after it only distances written in this iteration are on the critical
+// path.
 __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(DistArgs a) {
     const int rho = __ldcg(a.info);
     const int nsrc = __ldcg(a.off + 1);
     const long long max_iter = a.max_iter > 0 ? a.max_iter : 8LL * rho + 64;
     const int lane = threadIdx.x & 31;
-    const int gwarp = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const int wid = threadIdx.x >> 5;
+    const int gwarp = wid * gridDim.x + blockIdx.x;
     const int nwarps = (blockDim.x >> 5) * gridDim.x;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned tot_active = 0, tot_changed = 0, nfp64 = 0;
@@ -237,6 +272,8 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     __shared__ float s_max[DIST_THREADS / 32];
     __shared__ double s_sum[DIST_THREADS / 32];
     __shared__ int s_cnt[2][DIST_THREADS / 32];
+    __shared__ int2 s_queue[QUEUE_CAP];  // (vertex, bits of d_{k-1})
+    __shared__ int s_nq;
 
     auto off_at = [&](int r) { return __ldcg(a.off + (r < rho ? r : rho)); };
     Band bd;  // iteration 1: i_0 = 0, j_1 = min(1, rho - 1)
@@ -261,51 +298,90 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         float maxrel = 0.0f;
         double errsum = 0.0;
         const int base = start & ~31;
-        for (int c = gwarp;; c += nwarps) {
-            const int u = base + c * 32 + lane;
-            if (u - lane >= bd.hi) break;
-            if (u < start || u >= bd.hi) continue;
-            if (u < bd.lo) {  // retired after the previous iteration: keep both buffers equal
-                dnx[u] = __ldcg(dp + u);
-                continue;
-            }
-            if (u < nsrc) continue;  // sources stay 0
-            const float dold = __ldcg(dp + u);
-            const int ns = __ldcg(a.nstamp + u);
-            const int cg = __ldcg(a.chg + u);
-            const int meta = __ldg(a.meta + u);
-            const int4 r0 = __ldg(a.ring + 2 * u), r1 = __ldg(a.ring + 2 * u + 1);
-            const float3 x0 = xyz(__ldg(a.pos + u));
-            const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-            const bool need = (entering && u >= bd.vj_beg) || ns >= k - 1;
-            float dnew = dold;
-            if (need) {
-                if (meta & PTP_META_GENERAL) dnew = update_general(a, u, dold, dp, nfp64);
-                else dnew = update_ring(a, ids, x0, meta & PTP_META_CNT, dold, dp, nfp64);
-                ++n_active;
-            }
-            if (need || cg == k - 1) dnx[u] = dnew;
-            if (dnew != dold) {
-                ++n_changed;
-                a.chg[u] = (int)k;
-                if (meta & PTP_META_GENERAL) {
-                    stamp_general(a, u, (int)k);
-                } else {
-                    const int cnt = meta & PTP_META_CNT;
+        // chunks of this CTA's warps: c = gwarp + m * nwarps, m = 0, 1, ...
+        const int nchunks = bd.hi > base ? (bd.hi - base + 31) >> 5 : 0;
+        const int rounds_m = nchunks > gwarp ? (nchunks - gwarp + nwarps - 1) / nwarps : 0;
+        // every warp of the CTA must run the same number of rounds
+        const int cta_m = (nchunks > (int)blockIdx.x) ? (nchunks - (int)blockIdx.x + nwarps - 1) / nwarps : 0;
+        for (int m0 = 0; m0 < cta_m; m0 += ROUND_CHUNKS) {
+            if (threadIdx.x == 0) s_nq = 0;
+            __syncthreads();
+            // pass 1: state of each band vertex; queue the ones to recompute.
+            // The state of P1_BATCH chunks is loaded before any is used.
+            for (int m = m0; m < m0 + ROUND_CHUNKS && m < rounds_m; m += P1_BATCH) {
+                int uu[P1_BATCH], ns[P1_BATCH], cg[P1_BATCH];
+                float dold[P1_BATCH];
+                bool live[P1_BATCH];
 #pragma unroll
-                    for (int t = 0; t < PTP_RING; ++t)
-                        if (t < cnt) a.nstamp[ids[t]] = (int)k;
+                for (int q = 0; q < P1_BATCH; ++q) {
+                    uu[q] = base + (gwarp + (m + q) * nwarps) * 32 + lane;
+                    const bool ok = m + q < rounds_m && uu[q] >= start && uu[q] < bd.hi && uu[q] >= nsrc;
+                    live[q] = ok && uu[q] >= bd.lo;
+                    dold[q] = ok ? __ldcg(dp + uu[q]) : 0.0f;
+                    ns[q] = live[q] ? __ldcg(a.nstamp + uu[q]) : -2;
+                    cg[q] = live[q] ? __ldcg(a.chg + uu[q]) : -2;
+                    if (ok && !live[q]) dnx[uu[q]] = dold[q];  // retired after the previous iteration
+                }
+#pragma unroll
+                for (int q = 0; q < P1_BATCH; ++q) {
+                    const bool need = live[q] && ((entering && uu[q] >= bd.vj_beg) || ns[q] >= k - 1);
+                    if (live[q] && !need && cg[q] == k - 1) dnx[uu[q]] = dold[q];
+                    const unsigned bal = __ballot_sync(0xffffffffu, need);
+                    if (bal) {
+                        int at = 0;
+                        if (lane == 0) at = atomicAdd(&s_nq, __popc(bal));
+                        at = __shfl_sync(0xffffffffu, at, 0);
+                        if (need) s_queue[at + __popc(bal & ((1u << lane) - 1u))] = make_int2(uu[q], __float_as_int(dold[q]));
+                    }
                 }
             }
-            if (u < bd.vi_end) {
-                // relative-change test of Eq. lower_band, in FP64
-                const double o = dold, w = dnew, delta = fabs(w - o);
-                const bool ok = isfinite(o) && (delta == 0.0 || delta < a.eps * o + a.eps_abs);
-                if (!ok) notconv = 1;
-                const double rel = isfinite(o) ? (o > 0.0 ? delta / o : 0.0) : (double)INF;
-                maxrel = fmaxf(maxrel, (float)rel);
-                errsum += rel;
+            __syncthreads();
+            // pass 2: recompute the queued vertices
+            const int nq = s_nq;
+            for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+                const int2 ent = s_queue[q];
+                const int u = ent.x;
+                const float dold = __int_as_float(ent.y);
+                const int meta = __ldg(a.meta + u);
+                const int4 r0 = __ldg(a.ring + u), r1 = __ldg(a.ring + a.n + u);
+                const float4 l0 = __ldg(a.elen + u), l1 = __ldg(a.elen + a.n + u);
+                const int m = meta & PTP_META_CNT;
+                float4 g[PTP_TRI];
+#pragma unroll
+                for (int t = 0; t < PTP_TRI; ++t)
+                    g[t] = t < m - 1 ? __ldg(a.tgeom + (size_t)t * a.n + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+                float dnew;
+                if (meta & PTP_META_GENERAL) dnew = update_general(a, u, dold, dp, nfp64);
+                else dnew = update_ring(a, u, ids, el, g, m, dold, dp, nfp64);
+                ++n_active;
+                dnx[u] = dnew;
+                if (dnew != dold) {
+                    ++n_changed;
+                    a.chg[u] = (int)k;
+                    if (meta & PTP_META_GENERAL) {
+                        stamp_general(a, u, (int)k);
+                    } else {
+                        const int cnt = meta & PTP_META_CNT;
+#pragma unroll
+                        for (int t = 0; t < PTP_RING; ++t)
+                            if (t < cnt) a.nstamp[ids[t]] = (int)k;
+                    }
+                    if (u < bd.vi_end) {
+                        // relative-change test of Eq. lower_band, in FP64 (the
+                        // difference of two floats is exact in double)
+                        const double o = dold, delta = o - (double)dnew;
+                        if (!(isfinite(o) && delta < __dadd_rn(__dmul_rn(a.eps, o), a.eps_abs))) notconv = 1;
+                        if (a.trace) {
+                            const double rel = isfinite(o) ? (o > 0.0 ? delta / o : 0.0) : (double)INF;
+                            maxrel = fmaxf(maxrel, (float)rel);
+                            errsum += rel;
+                        }
+                    }
+                }
             }
+            __syncthreads();
         }
         tot_active += n_active;
         tot_changed += n_changed;
@@ -485,8 +561,11 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
         if (params->grid > 0 && params->grid < grid) grid = params->grid;
 
         DistArgs a;
+        a.n = (int)n;
         a.pos = t->pos;
         a.ring = t->ring;
+        a.tgeom = t->tgeom;
+        a.elen = t->elen;
         a.meta = t->meta;
         a.row = t->row;
         a.pairs = t->pairs;
@@ -629,8 +708,11 @@ extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params 
     if (params->grid > 0 && params->grid < grid) grid = params->grid;
 
     DistArgs a;
+    a.n = (int)n;
     a.pos = t->pos;
     a.ring = t->ring;
+    a.tgeom = t->tgeom;
+    a.elen = t->elen;
     a.meta = t->meta;
     a.row = t->row;
     a.pairs = t->pairs;

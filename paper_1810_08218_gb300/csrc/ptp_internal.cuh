@@ -60,6 +60,17 @@ struct ptp_ctrl {
 #define PTP_META_CLOSED 0x10
 #define PTP_META_GENERAL 0x20
 
+// Static per-triangle geometry of the one-ring slots, precomputed in FP64
+// and stored structure-of-arrays (component t of vertex u at [t * n + u]):
+//   tgeom[t] = (b, L, alpha, beta) of triangle t = (u, ring[t], ring[t+1]):
+//     e1 = x_ring[t] - x_u, e2 = x_ring[t+1] - x_u, a = |e1|^2, c = |e2|^2,
+//     b = e1.e2, A = |e2 - e1|^2, L = sqrt(A), det = |e1 x e2|^2,
+//     alpha = (a - b) / A, beta = sqrt(det) / A; beta < 0 marks a
+//     near-degenerate triangle (some angle with sin^2 < 1e-6), solved in FP64
+//     from the positions instead;
+//   elen[0], elen[1] = |x_ring[t] - x_u| for t = 0..3 and 4..7.
+#define PTP_TRI 7
+
 struct ptp_toplesets_s {
     ptp_mesh *mesh;
     int device;
@@ -74,8 +85,10 @@ struct ptp_toplesets_s {
     float4 *pos;     // [n] renumbered positions
     int *row;        // [n + 1] renumbered corner offsets
     int2 *pairs;     // [3 nf] renumbered corner pairs
-    int4 *ring;      // [2 n] one-ring slots
+    int4 *ring;      // [2 n] one-ring slots (ring[u], ring[n + u])
     int *meta;       // [n]
+    float4 *tgeom;   // [PTP_TRI n] per-triangle geometry, structure of arrays
+    float4 *elen;    // [2 n] edge lengths to the ring neighbours
     ptp_ctrl *ctrl;  // control block of the last ptp_distance run
 };
 

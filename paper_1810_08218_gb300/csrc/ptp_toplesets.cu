@@ -236,9 +236,61 @@ __global__ void build_rings(int n, const int *__restrict__ nrow, const int2 *__r
                 m = (deg + 1) | (open ? 0 : PTP_META_CLOSED);
             }
         }
-        ring[2 * u] = make_int4(r[0], r[1], r[2], r[3]);
-        ring[2 * u + 1] = make_int4(r[4], r[5], r[6], r[7]);
+        ring[u] = make_int4(r[0], r[1], r[2], r[3]);
+        ring[n + u] = make_int4(r[4], r[5], r[6], r[7]);
         meta[u] = m;
+    }
+}
+
+
+// Precompute the static geometry of every ring triangle in FP64 (see the
+// layout comment in ptp_internal.cuh), so the window kernel's update step
+// needs only the two neighbour distances per triangle.
+__global__ void build_geometry(int n, const float4 *__restrict__ pos, const int4 *__restrict__ ring,
+                               const int *__restrict__ meta, float4 *__restrict__ tgeom, float4 *__restrict__ elen) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const int m = meta[u];
+        const int4 r0 = ring[u], r1 = ring[n + u];
+        const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        const int cnt = (m & PTP_META_GENERAL) ? 0 : (m & PTP_META_CNT);
+        const float4 p0 = pos[u];
+        double ex[PTP_RING], ey[PTP_RING], ez[PTP_RING];
+        float el[PTP_RING];
+        for (int t = 0; t < PTP_RING; ++t) {
+            if (t < cnt) {
+                const float4 p = pos[ids[t]];
+                ex[t] = (double)p.x - p0.x;
+                ey[t] = (double)p.y - p0.y;
+                ez[t] = (double)p.z - p0.z;
+                el[t] = (float)sqrt(ex[t] * ex[t] + ey[t] * ey[t] + ez[t] * ez[t]);
+            } else {
+                ex[t] = ey[t] = ez[t] = 0.0;
+                el[t] = 0.0f;
+            }
+        }
+        elen[u] = make_float4(el[0], el[1], el[2], el[3]);
+        elen[n + u] = make_float4(el[4], el[5], el[6], el[7]);
+        for (int t = 0; t < PTP_TRI; ++t) {
+            float4 g = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+            if (t < cnt - 1) {
+                const double a = ex[t] * ex[t] + ey[t] * ey[t] + ez[t] * ez[t];
+                const double c = ex[t + 1] * ex[t + 1] + ey[t + 1] * ey[t + 1] + ez[t + 1] * ez[t + 1];
+                const double b = ex[t] * ex[t + 1] + ey[t] * ey[t + 1] + ez[t] * ez[t + 1];
+                const double fx = ex[t + 1] - ex[t], fy = ey[t + 1] - ey[t], fz = ez[t + 1] - ez[t];
+                const double A = fx * fx + fy * fy + fz * fz;
+                const double cx = ey[t] * ez[t + 1] - ez[t] * ey[t + 1];
+                const double cy = ez[t] * ex[t + 1] - ex[t] * ez[t + 1];
+                const double cz = ex[t] * ey[t + 1] - ey[t] * ex[t + 1];
+                const double det = cx * cx + cy * cy + cz * cz;
+                const double big = fmax(a * c, A * fmax(a, c));
+                const double amb = -(ex[t] * fx + ey[t] * fy + ez[t] * fz);  // a - b
+                if (A > 0.0 && det >= 1e-6 * big)
+                    g = make_float4((float)b, (float)sqrt(A), (float)(amb / A), (float)(sqrt(det) / A));
+                else
+                    g = make_float4((float)b, (float)sqrt(A), 0.0f, -1.0f);
+            }
+            tgeom[(size_t)t * n + u] = g;
+        }
     }
 }
 
@@ -302,6 +354,8 @@ extern "C" ptp_status ptp_toplesets(ptp_mesh *mesh, const int32_t *sources, int3
         TOPS_TRY(cudaMallocAsync((void **)&t->pairs, sizeof(int2) * t->ncorner, s));
         TOPS_TRY(cudaMallocAsync((void **)&t->ring, sizeof(int4) * 2 * n, s));
         TOPS_TRY(cudaMallocAsync((void **)&t->meta, sizeof(int) * n, s));
+        TOPS_TRY(cudaMallocAsync((void **)&t->tgeom, sizeof(float4) * PTP_TRI * n, s));
+        TOPS_TRY(cudaMallocAsync((void **)&t->elen, sizeof(float4) * 2 * n, s));
         TOPS_TRY(cudaMallocAsync((void **)&t->ctrl, sizeof(ptp_ctrl), s));
         // work: [0..n) degree in new order, then scan temp, then bfs counters
         const int64_t scan_tmp = ptp_scan_tmp_ints(n);
@@ -348,7 +402,8 @@ extern "C" ptp_status ptp_toplesets(ptp_mesh *mesh, const int32_t *sources, int3
         renumber_corners<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, t->iperm, (int)n, mesh->row, mesh->pairs, t->row,
                                                                 t->pairs);
         build_rings<<<blocks_for(n, 128, dev), 128, 0, s>>>((int)n, t->row, t->pairs, t->ring, t->meta);
-        ptp_count_launches(2);
+        build_geometry<<<blocks_for(n, 128, dev), 128, 0, s>>>((int)n, t->pos, t->ring, t->meta, t->tgeom, t->elen);
+        ptp_count_launches(3);
         TOPS_TRY(cudaGetLastError());
         cudaFreeAsync(work, s);
         cudaFreeAsync(src_d, s);
@@ -359,7 +414,8 @@ fail:
     if (work) cudaFreeAsync(work, s);
     if (src_d) cudaFreeAsync(src_d, s);
     {
-        void *ptrs[] = {t->level, t->perm, t->iperm, t->off, t->info, t->pos, t->row, t->pairs, t->ring, t->meta, t->ctrl};
+        void *ptrs[] = {t->level, t->perm, t->iperm, t->off, t->info, t->pos, t->row, t->pairs, t->ring, t->meta,
+                        t->tgeom, t->elen, t->ctrl};
         for (void *p : ptrs)
             if (p) cudaFreeAsync(p, s);
     }
@@ -385,7 +441,8 @@ extern "C" ptp_status ptp_toplesets_info(ptp_toplesets_t *t, void *stream, int32
 
 extern "C" ptp_status ptp_toplesets_destroy(ptp_toplesets_t *t) {
     if (!t) return PTP_ERR_ARG;
-    void *ptrs[] = {t->level, t->perm, t->iperm, t->off, t->info, t->pos, t->row, t->pairs, t->ring, t->meta, t->ctrl};
+    void *ptrs[] = {t->level, t->perm, t->iperm, t->off, t->info, t->pos, t->row, t->pairs, t->ring, t->meta,
+                    t->tgeom, t->elen, t->ctrl};
     for (void *p : ptrs)
         if (p) cudaFreeAsync(p, t->stream);
     const cudaError_t e = cudaStreamSynchronize(t->stream);
