@@ -33,6 +33,8 @@ struct ptp_mesh {
     int *row;             // [n + 1] corner offsets
     int2 *pairs;          // [3 nf] per corner: the other two vertices of the face,
                           //        in the face's cyclic order
+    int4 *ring;           // [2 n] one-ring slots, original numbering (layout below)
+    int *meta;            // [n]
     double diameter;      // bounding-box diagonal
 };
 

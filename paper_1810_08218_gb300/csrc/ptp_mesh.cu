@@ -1,7 +1,8 @@
 // Mesh construction: validation, the vertex -> incident-triangle lists
-// ("corner lists"), positions and the bounding-box diameter.  The paper keeps
-// the mesh as a compact half-edge structure (Sec. 3.3); the update step only
-// needs, per vertex, the triangles around it, which is what this builds.
+// ("corner lists"), the one-ring slots (fans in cyclic order), positions and
+// the bounding-box diameter.  The paper keeps the mesh as a compact half-edge
+// structure (Sec. 3.3); the update step only needs, per vertex, the
+// triangles around it, which is what this builds.
 #include <float.h>
 #include <math.h>
 #include <stdlib.h>
@@ -233,6 +234,97 @@ __global__ void init_bbox(int *bb) {
     else if (threadIdx.x < 6) bb[threadIdx.x] = (int)0x80000000;
 }
 
+// Order each vertex's incident triangles into a fan.  The link of u (the
+// edges {a, b} over its corners) must be one simple path (open fan, boundary
+// vertex) or one simple cycle (closed fan).  The walk along it gives deg + 1
+// entries r[0..deg]; for a cycle r[deg] == r[0], so in both cases triangle t
+// is (u, r[t], r[t+1]) for t < deg.  Vertices whose walk does not fit in
+// PTP_RING entries, or whose link is anything else (non-manifold, repeated
+// faces), are marked GENERAL and use the corner lists instead.
+__global__ void build_rings(int n, const int *__restrict__ nrow, const int2 *__restrict__ npairs, int4 *__restrict__ ring,
+                            int *__restrict__ meta) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const int cb = nrow[u];
+        const int deg = nrow[u + 1] - cb;
+        int r[PTP_RING];
+#pragma unroll
+        for (int q = 0; q < PTP_RING; ++q) r[q] = -1;
+        int m = 0;
+        if (deg + 1 > PTP_RING) {
+            m = PTP_META_GENERAL;
+        } else if (deg > 0) {
+            int pa[PTP_RING], pb[PTP_RING];
+            for (int q = 0; q < deg; ++q) {
+                const int2 pr = npairs[cb + q];
+                pa[q] = pr.x;
+                pb[q] = pr.y;
+            }
+            // the corner lists are filled by atomics in arbitrary order; sort
+            // them so the fan (and every FP32 result) is the same each run
+            for (int q = 1; q < deg; ++q) {
+                const int xa = pa[q], xb = pb[q];
+                int z = q - 1;
+                while (z >= 0 && (pa[z] > xa || (pa[z] == xa && pb[z] > xb))) {
+                    pa[z + 1] = pa[z];
+                    pb[z + 1] = pb[z];
+                    --z;
+                }
+                pa[z + 1] = xa;
+                pb[z + 1] = xb;
+            }
+            bool bad = false, open = false;
+            int start = 0, first = pa[0];
+            for (int q = 0; q < deg && !bad; ++q) {
+                for (int e = 0; e < 2; ++e) {
+                    const int x = e ? pb[q] : pa[q];
+                    int occ = 0;
+                    for (int t = 0; t < deg; ++t) occ += (pa[t] == x) + (pb[t] == x);
+                    if (occ > 2) bad = true;
+                    if (occ == 1 && !open) {
+                        open = true;
+                        start = q;
+                        first = x;
+                    }
+                }
+            }
+            if (!bad) {
+                unsigned used = 1u << start;
+                r[0] = first;
+                r[1] = pa[start] == first ? pb[start] : pa[start];
+                for (int step = 1; step < deg; ++step) {
+                    const int last = r[step];
+                    int found = -1;
+                    for (int t = 0; t < deg; ++t)
+                        if (!(used >> t & 1u) && (pa[t] == last || pb[t] == last)) { found = t; break; }
+                    if (found < 0) { bad = true; break; }
+                    used |= 1u << found;
+                    r[step + 1] = pa[found] == last ? pb[found] : pa[found];
+                }
+            }
+            if (!bad) {
+                // distinct entries, except that a cycle closes on r[0]
+                const int distinct = open ? deg + 1 : deg;
+                if (!open && r[deg] != r[0]) bad = true;
+                if (open && r[deg] == r[0]) bad = true;
+                for (int a = 0; a < distinct && !bad; ++a)
+                    for (int b = a + 1; b < distinct; ++b)
+                        if (r[a] == r[b]) { bad = true; break; }
+            }
+            if (bad) {
+                m = PTP_META_GENERAL;
+#pragma unroll
+                for (int q = 0; q < PTP_RING; ++q) r[q] = -1;
+            } else {
+                m = (deg + 1) | (open ? 0 : PTP_META_CLOSED);
+            }
+        }
+        ring[u] = make_int4(r[0], r[1], r[2], r[3]);
+        ring[n + u] = make_int4(r[4], r[5], r[6], r[7]);
+        meta[u] = m;
+    }
+}
+
+
 unsigned grid_for(int64_t work, int threads, int device) {
     int64_t b = (work + threads - 1) / threads;
     const int64_t cap = (int64_t)ptp_num_sms(device) * 16;
@@ -279,6 +371,8 @@ extern "C" ptp_status ptp_mesh_create(const float *xyz, int64_t n_verts, const i
     MESH_TRY(cudaMallocAsync((void **)&m->pos, sizeof(float4) * n_verts, s));
     MESH_TRY(cudaMallocAsync((void **)&m->row, sizeof(int) * (n_verts + 1), s));
     MESH_TRY(cudaMallocAsync((void **)&m->pairs, sizeof(int2) * nc, s));
+    MESH_TRY(cudaMallocAsync((void **)&m->ring, sizeof(int4) * 2 * n_verts, s));
+    MESH_TRY(cudaMallocAsync((void **)&m->meta, sizeof(int) * n_verts, s));
     MESH_TRY(cudaMallocAsync((void **)&deg, sizeof(int) * (2 * n_verts + 8), s));
     MESH_TRY(cudaMallocAsync((void **)&tmp, sizeof(int) * ptp_scan_tmp_ints(n_verts), s));
     err = deg + 2 * n_verts;  // [0] face errors, [2..7] bbox keys
@@ -317,7 +411,8 @@ extern "C" ptp_status ptp_mesh_create(const float *xyz, int64_t n_verts, const i
     if (st != PTP_OK) goto fail;
     MESH_TRY(cudaMemsetAsync(deg + n_verts, 0, sizeof(int) * n_verts, s));
     fill_corners<<<grid_for(n_faces, 256, dev), 256, 0, s>>>(F_d, n_faces, m->row, deg + n_verts, m->pairs);
-    ptp_count_launches(1);
+    build_rings<<<grid_for(n_verts, 128, dev), 128, 0, s>>>((int)n_verts, m->row, m->pairs, m->ring, m->meta);
+    ptp_count_launches(2);
     MESH_TRY(cudaGetLastError());
     if (ptr_kind == PTP_HOST) {
         cudaFreeAsync(xyz_d, s);
@@ -338,6 +433,8 @@ fail:
     if (m->pos) cudaFreeAsync(m->pos, s);
     if (m->row) cudaFreeAsync(m->row, s);
     if (m->pairs) cudaFreeAsync(m->pairs, s);
+    if (m->ring) cudaFreeAsync(m->ring, s);
+    if (m->meta) cudaFreeAsync(m->meta, s);
     cudaStreamSynchronize(s);
     free(m);
     return st;
@@ -357,6 +454,8 @@ extern "C" ptp_status ptp_mesh_destroy(ptp_mesh *m) {
     cudaFreeAsync(m->pos, m->stream);
     cudaFreeAsync(m->row, m->stream);
     cudaFreeAsync(m->pairs, m->stream);
+    cudaFreeAsync(m->ring, m->stream);
+    cudaFreeAsync(m->meta, m->stream);
     const cudaError_t e = cudaStreamSynchronize(m->stream);
     free(m);
     return e == cudaSuccess ? PTP_OK : ptp_internal_cuda_status(e);

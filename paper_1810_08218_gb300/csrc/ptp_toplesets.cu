@@ -1,10 +1,11 @@
 // Toplesets (Sec. 3.1, Definition: V_0 = S, V_r = the not yet visited
-// neighbours of V_{r-1}) by a level-synchronous breadth-first search in one
-// persistent cooperative kernel, and the renumbering of the mesh in topleset
+// neighbours of V_{r-1}) by a level-synchronous breadth-first search inside
+// one thread-block cluster, and the renumbering of the mesh in topleset
 // order (Sec. 3.3): the BFS queue itself is the new vertex order, so V_r
-// occupies the index range [off[r], off[r+1]).  The renumbered mesh is also
-// packed into fixed-size one-ring slots (cyclic neighbour order) for the
-// window kernel.
+// occupies the index range [off[r], off[r+1]).  The renumbered mesh gets
+// one-ring slots (remapped from the mesh's), corner lists for the vertices
+// that have no slot, and the precomputed geometry of every ring triangle.
+#include <cooperative_groups.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -12,116 +13,177 @@
 
 #include "ptp_internal.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace {
 
-constexpr int BFS_THREADS = 512;
+constexpr int BC_CLUSTER = 8;     // CTAs in the BFS cluster (portable maximum)
+constexpr int BC_THREADS = 1024;  // threads per CTA
+constexpr int BC_CAP = 12288;     // frontier entries per CTA list (two lists: 96 KiB)
 
 __global__ void bfs_seed(const int *__restrict__ src, int m, int *__restrict__ level, int *__restrict__ queue,
-                         int *__restrict__ info, int *__restrict__ tail) {
+                         int *__restrict__ info) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < m; s += gridDim.x * blockDim.x) {
         const int v = src[s];
-        if (atomicCAS(&level[v], -1, 0) == -1) {
-            queue[atomicAdd(&info[3], 1)] = v;
-            atomicAdd(tail, 1);
-        }
+        if (atomicCAS(&level[v], -1, 0) == -1) queue[atomicAdd(&info[3], 1)] = v;
     }
 }
 
-// Level-synchronous BFS.  Level r's frontier is queue[off[r] .. off[r+1]).
-// One lane per frontier vertex: it loads its corners, then the levels of all
-// corner vertices, then claims the unvisited ones (atomicCAS on level), all
-// as independent loads / atomics in flight together.  A warp appends its
-// claims with one atomicAdd on the queue tail, and the grid barrier returns
-// the number of vertices added, i.e. the size of the next frontier.
-__global__ void __launch_bounds__(BFS_THREADS) bfs_levels(const int *__restrict__ row, const int2 *__restrict__ pairs,
-                                                          int *__restrict__ level, int *__restrict__ queue,
-                                                          int *__restrict__ off, int *__restrict__ info,
-                                                          unsigned long long *bar, int *tail, int *abort_flag) {
-    const int lane = threadIdx.x & 31;
-    const int gwarp = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;
-    const int nwarps = (blockDim.x >> 5) * gridDim.x;
-    __shared__ unsigned s_added;
-    unsigned long long prev_hi[2] = {0ull, 0ull};
+// Level-synchronous BFS in one cluster.  Level r's frontier is V_r, held as
+// the concatenation of the CTAs' lists in shared memory (level 0 and any
+// overflow are in global memory).  Frontier entries are dealt out in groups
+// of 32 to warps interleaved across the CTAs, so every SM shares the work
+// whichever CTA discovered the entries; a lane reads its entry from the
+// owner's list through distributed shared memory, writes it to its
+// renumbered position queue[off[r] + t], loads the vertex's one-ring slot,
+// reads its neighbours' levels and claims the unvisited ones with
+// atomicCAS; claimed vertices (V_{r+1}) are appended to the lane's own CTA
+// list.  After the hardware cluster barrier every CTA reads all list
+// lengths through distributed shared memory; their prefix sums locate the
+// next level's entries.
+__global__ void __cluster_dims__(BC_CLUSTER, 1, 1) __launch_bounds__(BC_THREADS, 1)
+    bfs_cluster(const int4 *__restrict__ ring, const int *__restrict__ meta, const int *__restrict__ row,
+                const int2 *__restrict__ pairs, int n, int *__restrict__ level, int *__restrict__ queue,
+                int *__restrict__ off, int *__restrict__ info, int *__restrict__ spill, int *__restrict__ spill_cnt) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    extern __shared__ int s_list[];  // [2][BC_CAP]
+    __shared__ int s_cnt[2];
+    __shared__ int s_pref[BC_CLUSTER + 1];
+    __shared__ int s_spill;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nwarps_cl = BC_CLUSTER * (BC_THREADS / 32);
+    const int gw = wid * BC_CLUSTER + rank;  // warps interleaved across the CTAs
+    const bool leader = rank == 0 && threadIdx.x == 0;
     int fbeg = 0;
-    int fend = __ldcg(&info[3]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int total = __ldcg(&info[3]);  // V_0 = the unique sources, queue[0, m0)
+    int nsmem = 0;                 // frontier entries held in the CTAs' lists
+    if (leader) {
         off[0] = 0;
-        off[1] = fend;
+        off[1] = total;
+        spill_cnt[0] = spill_cnt[1] = spill_cnt[2] = 0;
     }
+    if (threadIdx.x == 0) s_cnt[0] = s_cnt[1] = 0;
+    cl.sync();
     for (int r = 0;; ++r) {
-        if (threadIdx.x == 0) s_added = 0;
+        const int b = r & 1;  // V_{r+1} goes to list b; V_r (r >= 1) is in list b ^ 1
+        if (threadIdx.x == 0) s_cnt[b] = 0;
+        if (leader) spill_cnt[(r + 1) % 3] = 0;  // last read before the previous barrier
         __syncthreads();
-        const int base = fbeg & ~31;
-        unsigned my_added = 0;
-        for (int ch = gwarp;; ch += nwarps) {
-            const int p0 = base + ch * 32;
-            if (p0 >= fend) break;
-            const int p = p0 + lane;
-            const bool valid = p >= fbeg && p < fend;
-            const int u = valid ? __ldcg(&queue[p]) : 0;
-            const int cb = valid ? __ldg(row + u) : 0;
-            const int deg = valid ? __ldg(row + u + 1) - cb : 0;
-            int w[2 * PTP_RING];
-            unsigned claimed = 0;
-            if (deg <= PTP_RING) {
-                int lv[2 * PTP_RING];
-#pragma unroll
-                for (int t = 0; t < PTP_RING; ++t) {
-                    const int2 pr = t < deg ? __ldg(pairs + cb + t) : make_int2(0, 0);
-                    w[2 * t] = pr.x;
-                    w[2 * t + 1] = pr.y;
-                }
-#pragma unroll
-                for (int t = 0; t < 2 * PTP_RING; ++t) lv[t] = t < 2 * deg ? __ldcg(level + w[t]) : 0;
-#pragma unroll
-                for (int t = 0; t < 2 * PTP_RING; ++t)
-                    if (lv[t] < 0 && atomicCAS(&level[w[t]], -1, r + 1) == -1) claimed |= 1u << t;
-            } else {
-                // rare high-valence vertex: claim and append one at a time
-                for (int c = cb; c < cb + deg; ++c) {
-                    const int2 pr = __ldg(pairs + c);
-                    const int ww[2] = {pr.x, pr.y};
-                    for (int e = 0; e < 2; ++e)
-                        if (__ldcg(level + ww[e]) < 0 && atomicCAS(&level[ww[e]], -1, r + 1) == -1) {
-                            queue[atomicAdd(tail, 1)] = ww[e];
-                            ++my_added;
-                        }
+        const int *spill_in = spill + (size_t)(b ^ 1) * n;
+        int *spill_out = spill + (size_t)b * n;
+        int *lst_out = s_list + b * BC_CAP;
+        const int steps = (total + 32 * nwarps_cl - 1) / (32 * nwarps_cl);
+        for (int step = 0; step < steps; ++step) {
+            const int t = (step * nwarps_cl + gw) * 32 + lane;
+            int u = -1;
+            if (t < total) {
+                if (r == 0) {
+                    u = __ldcg(&queue[t]);  // the sources are already in place
+                } else {
+                    if (t < nsmem) {
+                        int q = 0;
+                        while (q + 1 < BC_CLUSTER && s_pref[q + 1] <= t) ++q;
+                        const int *lst = cl.map_shared_rank(s_list + (b ^ 1) * BC_CAP, q);
+                        u = lst[t - s_pref[q]];
+                    } else {
+                        u = __ldcg(&spill_in[t - nsmem]);
+                    }
+                    queue[fbeg + t] = u;  // renumbered position of u
                 }
             }
-            // warp-aggregated append of the claimed vertices
-            const int cnt = __popc(claimed);
-            int incl = cnt;
+            int w[PTP_RING];
+            unsigned claimed = 0;
+            const int m = u >= 0 ? __ldg(meta + u) : PTP_META_GENERAL;
+            const int4 r0 = u >= 0 ? __ldg(ring + u) : make_int4(-1, -1, -1, -1);
+            const int4 r1 = u >= 0 ? __ldg(ring + n + u) : make_int4(-1, -1, -1, -1);
+            if (u >= 0 && !(m & PTP_META_GENERAL)) {
+                const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                const int cnt = m & PTP_META_CNT;
+                // read the neighbours' levels first (plain loads, all in
+                // flight), then claim only the unvisited ones
+                int lv[PTP_RING];
+#pragma unroll
+                for (int q = 0; q < PTP_RING; ++q) {
+                    w[q] = ids[q];
+                    lv[q] = q < cnt ? __ldcg(&level[ids[q]]) : 0;
+                }
+                int old[PTP_RING];
+#pragma unroll
+                for (int q = 0; q < PTP_RING; ++q) old[q] = lv[q] < 0 ? atomicCAS(&level[ids[q]], -1, r + 1) : 0;
+#pragma unroll
+                for (int q = 0; q < PTP_RING; ++q)
+                    if (lv[q] < 0 && old[q] == -1) claimed |= 1u << q;
+            } else if (u >= 0) {
+                // vertex without a ring slot: claim from its corner list, one at a time
+                const int cb = __ldg(row + u), ce = __ldg(row + u + 1);
+                for (int c = cb; c < ce; ++c) {
+                    const int2 pr = __ldg(pairs + c);
+                    const int ww[2] = {pr.x, pr.y};
+                    for (int e = 0; e < 2; ++e) {
+                        if (atomicCAS(&level[ww[e]], -1, r + 1) == -1) {
+                            const int at = atomicAdd(&s_cnt[b], 1);
+                            if (at < BC_CAP) lst_out[at] = ww[e];
+                            else spill_out[atomicAdd(&spill_cnt[r % 3], 1)] = ww[e];
+                        }
+                    }
+                }
+            }
+            // append the claimed ring neighbours, one shared atomic per warp
+            const int cntc = __popc(claimed);
+            int incl = cntc;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
-            const int total = __shfl_sync(0xffffffffu, incl, 31);
-            if (total) {
+            const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+            if (wtot) {
                 int at = 0;
-                if (lane == 31) at = atomicAdd(tail, total);
-                at = __shfl_sync(0xffffffffu, at, 31) + incl - cnt;
+                if (lane == 31) at = atomicAdd(&s_cnt[b], wtot);
+                at = __shfl_sync(0xffffffffu, at, 31) + incl - cntc;
 #pragma unroll
-                for (int t = 0; t < 2 * PTP_RING; ++t)
-                    if (claimed >> t & 1u) queue[at++] = w[t];
-                if (lane == 0) my_added += (unsigned)total;
+                for (int q = 0; q < PTP_RING; ++q) {
+                    if (claimed >> q & 1u) {
+                        if (at < BC_CAP) lst_out[at] = w[q];
+                        else spill_out[atomicAdd(&spill_cnt[r % 3], 1)] = w[q];
+                        ++at;
+                    }
+                }
             }
         }
-        if (my_added) atomicAdd(&s_added, my_added);
+        cl.sync();  // V_{r+1} complete in the lists and the spill buffer
+        if (threadIdx.x < 32) {
+            // one lane per cluster CTA reads its list length (distributed shared memory)
+            const int c = lane < BC_CLUSTER ? *cl.map_shared_rank(&s_cnt[b], lane) : 0;
+            const int over = __any_sync(0xffffffffu, c > BC_CAP);
+            int incl = c < BC_CAP ? c : BC_CAP;
+#pragma unroll
+            for (int o = 1; o < BC_CLUSTER; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane < BC_CLUSTER) s_pref[lane + 1] = incl;
+            if (lane == 0) {
+                s_pref[0] = 0;
+                s_spill = over ? __ldcg(&spill_cnt[r % 3]) : 0;
+            }
+        }
         __syncthreads();
-        const long long added = ptp_grid_sync(bar, r + 1, s_added, abort_flag, &info[2], prev_hi);
-        if (added < 0) return;
-        if (added == 0) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                info[0] = r + 1;  // rho
-                info[1] = fend;   // reached
+        const int next = s_pref[BC_CLUSTER] + s_spill;
+        if (next == 0) {
+            if (leader) {
+                info[0] = r + 1;          // rho
+                info[1] = fbeg + total;   // reached
             }
-            return;
+            break;
         }
-        fbeg = fend;
-        fend += (int)added;
-        if (blockIdx.x == 0 && threadIdx.x == 0) off[r + 2] = fend;
+        fbeg += total;
+        total = next;
+        nsmem = s_pref[BC_CLUSTER];
+        if (leader) off[r + 2] = fbeg + total;
     }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 // Append the vertices the BFS did not reach after the last topleset.
@@ -142,13 +204,27 @@ __global__ void append_unreached(const int *__restrict__ level, int n, int *__re
     }
 }
 
-__global__ void invert_perm(const int *__restrict__ perm, int n, int *__restrict__ iperm, const float4 *__restrict__ pos,
-                            float4 *__restrict__ npos, const int *__restrict__ row, int *__restrict__ ndeg) {
+__global__ void invert_perm(const int *__restrict__ perm, int n, int *__restrict__ iperm) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) iperm[perm[u]] = u;
+}
+
+// Renumbered positions, one-ring slots (ids remapped) and metadata; corner
+// counts only for the vertices without a slot (their corner lists are kept).
+__global__ void renumber_vertices(const int *__restrict__ perm, const int *__restrict__ iperm, int n,
+                                  const float4 *__restrict__ pos, const int4 *__restrict__ ring,
+                                  const int *__restrict__ meta, const int *__restrict__ row, float4 *__restrict__ npos,
+                                  int4 *__restrict__ nring, int *__restrict__ nmeta, int *__restrict__ ndeg) {
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
         const int v = perm[u];
-        iperm[v] = u;
         npos[u] = pos[v];
-        ndeg[u] = row[v + 1] - row[v];
+        const int m = meta[v];
+        nmeta[u] = m;
+        const int4 r0 = ring[v], r1 = ring[n + v];
+        const int cnt = (m & PTP_META_GENERAL) ? 0 : (m & PTP_META_CNT);
+        auto mp = [&](int q, int x) { return q < cnt ? iperm[x] : -1; };
+        nring[u] = make_int4(mp(0, r0.x), mp(1, r0.y), mp(2, r0.z), mp(3, r0.w));
+        nring[n + u] = make_int4(mp(4, r1.x), mp(5, r1.y), mp(6, r1.z), mp(7, r1.w));
+        ndeg[u] = (m & PTP_META_GENERAL) ? row[v + 1] - row[v] : 0;
     }
 }
 
@@ -156,8 +232,10 @@ __global__ void renumber_corners(const int *__restrict__ perm, const int *__rest
                                  const int *__restrict__ row, const int2 *__restrict__ pairs,
                                  const int *__restrict__ nrow, int2 *__restrict__ npairs) {
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        const int nb = nrow[u];
+        if (nrow[u + 1] == nb) continue;
         const int v = perm[u];
-        const int cb = row[v], ce = row[v + 1], nb = nrow[u];
+        const int cb = row[v], ce = row[v + 1];
         for (int c = cb; c < ce; ++c) {
             const int2 pr = pairs[c];
             npairs[nb + (c - cb)] = make_int2(iperm[pr.x], iperm[pr.y]);
@@ -165,87 +243,14 @@ __global__ void renumber_corners(const int *__restrict__ perm, const int *__rest
     }
 }
 
-// Order each vertex's incident triangles into a fan.  The link of u (the
-// edges {a, b} over its corners) must be one simple path (open fan, boundary
-// vertex) or one simple cycle (closed fan).  The walk along it gives deg + 1
-// entries r[0..deg]; for a cycle r[deg] == r[0], so in both cases triangle t
-// is (u, r[t], r[t+1]) for t < deg.  Vertices whose walk does not fit in
-// PTP_RING entries, or whose link is anything else (non-manifold, repeated
-// faces), are marked GENERAL and use the corner lists instead.
-__global__ void build_rings(int n, const int *__restrict__ nrow, const int2 *__restrict__ npairs, int4 *__restrict__ ring,
-                            int *__restrict__ meta) {
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
-        const int cb = nrow[u];
-        const int deg = nrow[u + 1] - cb;
-        int r[PTP_RING];
-#pragma unroll
-        for (int q = 0; q < PTP_RING; ++q) r[q] = -1;
-        int m = 0;
-        if (deg + 1 > PTP_RING) {
-            m = PTP_META_GENERAL;
-        } else if (deg > 0) {
-            int pa[PTP_RING], pb[PTP_RING];
-            for (int q = 0; q < deg; ++q) {
-                const int2 pr = npairs[cb + q];
-                pa[q] = pr.x;
-                pb[q] = pr.y;
-            }
-            bool bad = false, open = false;
-            int start = 0, first = pa[0];
-            for (int q = 0; q < deg && !bad; ++q) {
-                for (int e = 0; e < 2; ++e) {
-                    const int x = e ? pb[q] : pa[q];
-                    int occ = 0;
-                    for (int t = 0; t < deg; ++t) occ += (pa[t] == x) + (pb[t] == x);
-                    if (occ > 2) bad = true;
-                    if (occ == 1 && !open) {
-                        open = true;
-                        start = q;
-                        first = x;
-                    }
-                }
-            }
-            if (!bad) {
-                unsigned used = 1u << start;
-                r[0] = first;
-                r[1] = pa[start] == first ? pb[start] : pa[start];
-                for (int step = 1; step < deg; ++step) {
-                    const int last = r[step];
-                    int found = -1;
-                    for (int t = 0; t < deg; ++t)
-                        if (!(used >> t & 1u) && (pa[t] == last || pb[t] == last)) { found = t; break; }
-                    if (found < 0) { bad = true; break; }
-                    used |= 1u << found;
-                    r[step + 1] = pa[found] == last ? pb[found] : pa[found];
-                }
-            }
-            if (!bad) {
-                // distinct entries, except that a cycle closes on r[0]
-                const int distinct = open ? deg + 1 : deg;
-                if (!open && r[deg] != r[0]) bad = true;
-                if (open && r[deg] == r[0]) bad = true;
-                for (int a = 0; a < distinct && !bad; ++a)
-                    for (int b = a + 1; b < distinct; ++b)
-                        if (r[a] == r[b]) { bad = true; break; }
-            }
-            if (bad) {
-                m = PTP_META_GENERAL;
-#pragma unroll
-                for (int q = 0; q < PTP_RING; ++q) r[q] = -1;
-            } else {
-                m = (deg + 1) | (open ? 0 : PTP_META_CLOSED);
-            }
-        }
-        ring[u] = make_int4(r[0], r[1], r[2], r[3]);
-        ring[n + u] = make_int4(r[4], r[5], r[6], r[7]);
-        meta[u] = m;
-    }
-}
-
-
-// Precompute the static geometry of every ring triangle in FP64 (see the
-// layout comment in ptp_internal.cuh), so the window kernel's update step
-// needs only the two neighbour distances per triangle.
+// Precompute the static geometry of every ring triangle (see the layout
+// comment in ptp_internal.cuh), so the window kernel's update step needs only
+// the two neighbour distances per triangle.  Edge vectors are FP32
+// differences of nearby coordinates; the dot products, the cross product
+// and the derived terms are FP32, accurate to a few ulps for triangles that
+// are not near-degenerate (the update's own result is rounded to FP32
+// anyway); triangles close to the degeneracy threshold are classified in
+// FP64.
 __global__ void build_geometry(int n, const float4 *__restrict__ pos, const int4 *__restrict__ ring,
                                const int *__restrict__ meta, float4 *__restrict__ tgeom, float4 *__restrict__ elen) {
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
@@ -254,40 +259,50 @@ __global__ void build_geometry(int n, const float4 *__restrict__ pos, const int4
         const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
         const int cnt = (m & PTP_META_GENERAL) ? 0 : (m & PTP_META_CNT);
         const float4 p0 = pos[u];
-        double ex[PTP_RING], ey[PTP_RING], ez[PTP_RING];
+        float3 e[PTP_RING];
         float el[PTP_RING];
+#pragma unroll
         for (int t = 0; t < PTP_RING; ++t) {
             if (t < cnt) {
                 const float4 p = pos[ids[t]];
-                ex[t] = (double)p.x - p0.x;
-                ey[t] = (double)p.y - p0.y;
-                ez[t] = (double)p.z - p0.z;
-                el[t] = (float)sqrt(ex[t] * ex[t] + ey[t] * ey[t] + ez[t] * ez[t]);
+                e[t] = make_float3(p.x - p0.x, p.y - p0.y, p.z - p0.z);
+                el[t] = sqrtf(e[t].x * e[t].x + e[t].y * e[t].y + e[t].z * e[t].z);
             } else {
-                ex[t] = ey[t] = ez[t] = 0.0;
+                e[t] = make_float3(0.0f, 0.0f, 0.0f);
                 el[t] = 0.0f;
             }
         }
         elen[u] = make_float4(el[0], el[1], el[2], el[3]);
         elen[n + u] = make_float4(el[4], el[5], el[6], el[7]);
+#pragma unroll
         for (int t = 0; t < PTP_TRI; ++t) {
             float4 g = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
             if (t < cnt - 1) {
-                const double a = ex[t] * ex[t] + ey[t] * ey[t] + ez[t] * ez[t];
-                const double c = ex[t + 1] * ex[t + 1] + ey[t + 1] * ey[t + 1] + ez[t + 1] * ez[t + 1];
-                const double b = ex[t] * ex[t + 1] + ey[t] * ey[t + 1] + ez[t] * ez[t + 1];
-                const double fx = ex[t + 1] - ex[t], fy = ey[t + 1] - ey[t], fz = ez[t + 1] - ez[t];
-                const double A = fx * fx + fy * fy + fz * fz;
-                const double cx = ey[t] * ez[t + 1] - ez[t] * ey[t + 1];
-                const double cy = ez[t] * ex[t + 1] - ex[t] * ez[t + 1];
-                const double cz = ex[t] * ey[t + 1] - ey[t] * ex[t + 1];
-                const double det = cx * cx + cy * cy + cz * cz;
-                const double big = fmax(a * c, A * fmax(a, c));
-                const double amb = -(ex[t] * fx + ey[t] * fy + ez[t] * fz);  // a - b
-                if (A > 0.0 && det >= 1e-6 * big)
-                    g = make_float4((float)b, (float)sqrt(A), (float)(amb / A), (float)(sqrt(det) / A));
-                else
-                    g = make_float4((float)b, (float)sqrt(A), 0.0f, -1.0f);
+                const float3 e1 = e[t], e2 = e[t + 1];
+                const float3 f = make_float3(e2.x - e1.x, e2.y - e1.y, e2.z - e1.z);
+                const float a = e1.x * e1.x + e1.y * e1.y + e1.z * e1.z;
+                const float c = e2.x * e2.x + e2.y * e2.y + e2.z * e2.z;
+                const float b = e1.x * e2.x + e1.y * e2.y + e1.z * e2.z;
+                const float A = f.x * f.x + f.y * f.y + f.z * f.z;
+                const float cx = e1.y * e2.z - e1.z * e2.y, cy = e1.z * e2.x - e1.x * e2.z, cz = e1.x * e2.y - e1.y * e2.x;
+                const float det = cx * cx + cy * cy + cz * cz;
+                const float big = fmaxf(a * c, A * fmaxf(a, c));
+                bool ok = A > 0.0f && det >= 1e-6f * big;
+                if (A > 0.0f && det < 1e-4f * big) {
+                    // close to the threshold: decide it in FP64
+                    const double dx = (double)e1.y * e2.z - (double)e1.z * e2.y;
+                    const double dy = (double)e1.z * e2.x - (double)e1.x * e2.z;
+                    const double dz = (double)e1.x * e2.y - (double)e1.y * e2.x;
+                    const double dd = dx * dx + dy * dy + dz * dz;
+                    const double ad = (double)e1.x * e1.x + (double)e1.y * e1.y + (double)e1.z * e1.z;
+                    const double cd = (double)e2.x * e2.x + (double)e2.y * e2.y + (double)e2.z * e2.z;
+                    const double fx = (double)e2.x - e1.x, fy = (double)e2.y - e1.y, fz = (double)e2.z - e1.z;
+                    const double Ad = fx * fx + fy * fy + fz * fz;
+                    ok = dd >= 1e-6 * fmax(ad * cd, Ad * fmax(ad, cd));
+                }
+                const float amb = -(e1.x * f.x + e1.y * f.y + e1.z * f.z);  // a - b
+                const float L = sqrtf(A);
+                g = ok ? make_float4(b, L, amb / A, sqrtf(det) / A) : make_float4(b, L, 0.0f, -1.0f);
             }
             tgeom[(size_t)t * n + u] = g;
         }
@@ -351,59 +366,51 @@ extern "C" ptp_status ptp_toplesets(ptp_mesh *mesh, const int32_t *sources, int3
         TOPS_TRY(cudaMallocAsync((void **)&t->info, sizeof(int) * 4, s));
         TOPS_TRY(cudaMallocAsync((void **)&t->pos, sizeof(float4) * n, s));
         TOPS_TRY(cudaMallocAsync((void **)&t->row, sizeof(int) * (n + 1), s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->pairs, sizeof(int2) * t->ncorner, s));
         TOPS_TRY(cudaMallocAsync((void **)&t->ring, sizeof(int4) * 2 * n, s));
         TOPS_TRY(cudaMallocAsync((void **)&t->meta, sizeof(int) * n, s));
         TOPS_TRY(cudaMallocAsync((void **)&t->tgeom, sizeof(float4) * PTP_TRI * n, s));
         TOPS_TRY(cudaMallocAsync((void **)&t->elen, sizeof(float4) * 2 * n, s));
         TOPS_TRY(cudaMallocAsync((void **)&t->ctrl, sizeof(ptp_ctrl), s));
-        // work: [0..n) degree in new order, then scan temp, then bfs counters
+        // work: counters [0..15], degrees [n], scan temp, BFS spill lists [2n]
         const int64_t scan_tmp = ptp_scan_tmp_ints(n);
-        TOPS_TRY(cudaMallocAsync((void **)&work, sizeof(int) * (n + scan_tmp + 16), s));
-        // counters first so the 64-bit barrier words are 8-byte aligned:
-        // [0] queue tail, [3] abort, [4] unreached counter, [8..11] barrier words
-        int *bfs_cnt = work;
-        unsigned long long *bfs_bar = (unsigned long long *)(bfs_cnt + 8);
+        TOPS_TRY(cudaMallocAsync((void **)&work, sizeof(int) * (16 + n + scan_tmp + 2 * n), s));
+        int *cnt = work;  // [0..2] spill counters, [4] unreached counter
         int *ndeg = work + 16;
         int *tmp = ndeg + n;
+        int *spill = tmp + scan_tmp;
 
         TOPS_TRY(cudaMallocAsync((void **)&src_d, sizeof(int) * m, s));
         TOPS_TRY(cudaMemcpyAsync(src_d, hsrc.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
         TOPS_TRY(cudaMemsetAsync(t->level, 0xFF, sizeof(int) * n, s));
         TOPS_TRY(cudaMemsetAsync(t->info, 0, sizeof(int) * 4, s));
         TOPS_TRY(cudaMemsetAsync(t->off, 0, sizeof(int) * (n + 2), s));
-        TOPS_TRY(cudaMemsetAsync(bfs_cnt, 0, sizeof(int) * 16, s));
+        TOPS_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * 16, s));
         TOPS_TRY(cudaMemsetAsync(t->ctrl, 0, sizeof(ptp_ctrl), s));
-        bfs_seed<<<blocks_for(m, 256, dev), 256, 0, s>>>(src_d, m, t->level, t->perm, t->info, bfs_cnt);
+        bfs_seed<<<blocks_for(m, 256, dev), 256, 0, s>>>(src_d, m, t->level, t->perm, t->info);
         ptp_count_launches(1);
         TOPS_TRY(cudaGetLastError());
-
-        // persistent BFS: every CTA co-resident
-        int per_sm = 0;
-        TOPS_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_levels, BFS_THREADS, 0));
-        if (per_sm < 1) { st = PTP_ERR_CUDA; goto fail; }
-        int nblk = per_sm * ptp_num_sms(dev);
         {
-            const int *row_c = mesh->row;
-            const int2 *pairs_c = mesh->pairs;
-            int *tail = bfs_cnt;
-            int *abort_flag = bfs_cnt + 3;
-            void *args[] = {(void *)&row_c, (void *)&pairs_c, (void *)&t->level, (void *)&t->perm, (void *)&t->off,
-                            (void *)&t->info, (void *)&bfs_bar, (void *)&tail, (void *)&abort_flag};
-            TOPS_TRY(cudaLaunchCooperativeKernel((const void *)bfs_levels, dim3(nblk), dim3(BFS_THREADS), args, 0, s));
+            const size_t smem = sizeof(int) * 2 * BC_CAP;
+            TOPS_TRY(cudaFuncSetAttribute(bfs_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            bfs_cluster<<<BC_CLUSTER, BC_THREADS, smem, s>>>(mesh->ring, mesh->meta, mesh->row, mesh->pairs, (int)n,
+                                                             t->level, t->perm, t->off, t->info, spill, cnt);
             ptp_count_launches(1);
+            TOPS_TRY(cudaGetLastError());
         }
-        append_unreached<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->level, (int)n, t->perm, t->info, bfs_cnt + 4);
-        invert_perm<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, t->iperm, mesh->pos, t->pos, mesh->row, ndeg);
-        ptp_count_launches(2);
+        append_unreached<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->level, (int)n, t->perm, t->info, cnt + 4);
+        invert_perm<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, t->iperm);
+        renumber_vertices<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, t->iperm, (int)n, mesh->pos, mesh->ring,
+                                                                 mesh->meta, mesh->row, t->pos, t->ring, t->meta, ndeg);
+        ptp_count_launches(3);
         TOPS_TRY(cudaGetLastError());
         st = ptp_exclusive_scan(ndeg, t->row, n, tmp, s);
         if (st != PTP_OK) goto fail;
-        renumber_corners<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, t->iperm, (int)n, mesh->row, mesh->pairs, t->row,
-                                                                t->pairs);
-        build_rings<<<blocks_for(n, 128, dev), 128, 0, s>>>((int)n, t->row, t->pairs, t->ring, t->meta);
+        // corner lists, filled only for the vertices without a ring slot
+        TOPS_TRY(cudaMallocAsync((void **)&t->pairs, sizeof(int2) * t->ncorner, s));
+        renumber_corners<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, t->iperm, (int)n, mesh->row, mesh->pairs,
+                                                                t->row, t->pairs);
         build_geometry<<<blocks_for(n, 128, dev), 128, 0, s>>>((int)n, t->pos, t->ring, t->meta, t->tgeom, t->elen);
-        ptp_count_launches(3);
+        ptp_count_launches(2);
         TOPS_TRY(cudaGetLastError());
         cudaFreeAsync(work, s);
         cudaFreeAsync(src_d, s);
