@@ -68,6 +68,10 @@ typedef struct ptp_params {
     int64_t max_iter;  /* iteration cap; 0 = 8 * rho + 64                          */
     int32_t block;     /* threads per CTA of the window kernel; 0 = auto           */
     int32_t grid;      /* CTAs of the window kernel; 0 = all co-resident CTAs      */
+    int32_t band_mode; /* 0: the paper's dynamic band (Eq. lower_band); 1: the
+                          fixed band of the complexity analysis (Sec. 5), lower
+                          bound ceil(k / 2), no convergence test                   */
+    int32_t reserved;  /* must be 0                                                */
     void *trace;       /* optional DEVICE buffer of trace_cap ptp_trace_rec, one per
                           iteration, or NULL                                       */
     int64_t trace_cap;
@@ -101,7 +105,8 @@ typedef struct ptp_stats {
 const char *ptp_status_str(ptp_status s);
 
 /* Defaults: eps = 1e-3 and eps_abs = 0 (Sec. 3.2, the paper's setting),
- * max_iter = 0 (auto), block = grid = 0 (auto), no trace, no events. */
+ * max_iter = 0 (auto), block = grid = 0 (auto), band_mode = 0, no trace, no
+ * events. */
 ptp_status ptp_params_default(ptp_params *p);
 
 /* Number of CUDA kernel launches this library has issued in this process
@@ -207,6 +212,39 @@ ptp_status ptp_distance(ptp_toplesets_t *tops, const ptp_params *params, float *
 #define PTP_NOALLOC_MAX_VERTS 1048576
 ptp_status ptp_distance_noalloc(ptp_toplesets_t *tops, const ptp_params *params, float *d_out, void *stream,
                                 ptp_stats *stats);
+
+/*
+ * Geodesic Voronoi regions (Sec. 4.3, Voronoi diagrams from farthest-point
+ * samples): one multi-source PTP map from the m seeds (Sec. 3.4, multi-source
+ * problem; as in the paper's multi-source runs the vertices are not
+ * rearranged), where every vertex also carries the index (0..m-1) of the seed
+ * its distance came from: the label of the closer neighbour of the triangle
+ * that gave its final value.
+ *  seeds      [m] vertex indices (ptr_kind), m >= 1; a repeated seed keeps its
+ *             first index.
+ *  d_out      [n_verts] float32 DEVICE, distance to the nearest seed.
+ *  label_out  [n_verts] int32 DEVICE, seed index, -1 where unreachable.
+ *  Blocks only when stats is non-NULL (as ptp_distance).
+ */
+ptp_status ptp_voronoi(ptp_mesh *mesh, const int32_t *seeds, int32_t m, int ptr_kind, const ptp_params *params,
+                       float *d_out, int32_t *label_out, void *stream, ptp_stats *stats);
+
+/*
+ * Farthest-point sampling (Sec. 4.3 and App. A): S_1 = {first};
+ * S_{i+1} = S_i + argmax_v d_{S_i}(v), each d_{S_i} a full multi-source PTP
+ * map from all samples so far (ties: the smallest vertex index; an
+ * unreachable vertex counts as infinitely far).  Everything stays on the
+ * device: the argmax, the sample list and the source count are device data,
+ * and with use_graph != 0 one sampling step is captured once as a CUDA graph
+ * and relaunched for every sample.
+ *  samples_out  [n_samples] int32 DEVICE: first, then the chosen samples.
+ *  d_out        [n_verts] float32 DEVICE or NULL: distance to all n_samples
+ *               samples (one more map).
+ *  stats        NULL or totals over all maps (iterations, updates; rho of the
+ *               last map; status = the worst status seen).  Blocks.
+ */
+ptp_status ptp_fps(ptp_mesh *mesh, int32_t first, int32_t n_samples, const ptp_params *params, int32_t *samples_out,
+                   float *d_out, int use_graph, void *stream, ptp_stats *stats);
 
 /* Statistics of the last ptp_distance call on this handle.  Blocks on
  * `stream`.  Returns that call's device-side status. */

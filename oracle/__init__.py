@@ -59,7 +59,7 @@ def _load():
             lib.or_toplesets.restype = i64
             lib.or_toplesets.argtypes = [i64, P, P, P, i32, P, P]
             lib.or_ptp.restype = ctypes.c_int
-            lib.or_ptp.argtypes = [i64, P, i64, P, i32, P, dbl, dbl, i64, P, P, P, P, P, i64, P, i64]
+            lib.or_ptp.argtypes = [i64, P, i64, P, i32, P, dbl, dbl, i64, ctypes.c_int, P, P, P, P, P, i64, P, i64]
             lib.or_relax.restype = i64
             lib.or_relax.argtypes = [i64, P, i64, P, i32, P, ctypes.c_int, ctypes.c_uint64, i64, P]
             _lib = lib
@@ -120,9 +120,10 @@ class PTPResult:
 
 
 def ptp(V: np.ndarray, F: np.ndarray, sources, eps: float = 1e-3, eps_abs: float = 0.0,
-        max_iter: int = 0, trace: bool = False, history: int = 0) -> PTPResult:
+        max_iter: int = 0, trace: bool = False, history: int = 0, band_mode: int = 0) -> PTPResult:
     """Run the oracle PTP (Sec. 3.2) in FP64.  `history` > 0 keeps d_k for
-    k = 0 .. history-1 (tiny meshes only)."""
+    k = 0 .. history-1 (tiny meshes only).  band_mode 1: the fixed band of
+    the complexity analysis (Sec. 5) instead of Eq. lower_band."""
     lib = _load()
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)
@@ -139,7 +140,7 @@ def ptp(V: np.ndarray, F: np.ndarray, sources, eps: float = 1e-3, eps_abs: float
         tm = np.zeros(cap, dtype=np.float64)
     hist = np.zeros((history, n), dtype=np.float64) if history > 0 else None
     rc = lib.or_ptp(n, _ptr(V), F.shape[0], _ptr(F), src.shape[0], _ptr(src), float(eps), float(eps_abs),
-                    int(max_iter), _ptr(d), _ptr(stats),
+                    int(max_iter), int(band_mode), _ptr(d), _ptr(stats),
                     _ptr(ti) if ti is not None else None, _ptr(tj) if tj is not None else None,
                     _ptr(tm) if tm is not None else None, cap,
                     _ptr(hist) if hist is not None else None, history)

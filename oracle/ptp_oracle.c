@@ -215,11 +215,14 @@ static void update_vertex_all(int64_t v, const double *xyz, const int64_t *row, 
  * trace_j[k-1] = j_k, trace_maxrel[k-1] = max relative change on V_{i_{k-1}}.
  * Optional history: d_hist[k*n + v] = d_k(v) for k = 0 .. hist_cap-1.
  * max_iter <= 0 means 8*rho + 64.
+ * band_mode 1 replaces Eq. lower_band by the fixed band of the complexity
+ * analysis (Sec. 5: the band holds the last k/2 toplesets), i.e. the lower
+ * bound after iteration k is ceil(k/2), with no convergence test.
  * Returns OR_OK, OR_NOT_CONVERGED (max_iter reached, d_out still written)
  * or a negative error.
  */
 int or_ptp(int64_t n, const double *xyz, int64_t nf, const int32_t *faces, int32_t m,
-           const int32_t *src, double eps, double eps_abs, int64_t max_iter, double *d_out,
+           const int32_t *src, double eps, double eps_abs, int64_t max_iter, int band_mode, double *d_out,
            int64_t *stats, int32_t *trace_i, int32_t *trace_j, double *trace_maxrel,
            int64_t trace_cap, double *d_hist, int64_t hist_cap) {
     if (n <= 0 || nf <= 0 || m <= 0 || !xyz || !faces || !src || !d_out) return OR_ERR_ARG;
@@ -305,6 +308,7 @@ int or_ptp(int64_t n, const double *xyz, int64_t nf, const int32_t *faces, int32
             if (trace_maxrel) trace_maxrel[k - 1] = maxrel;
         }
         if (d_hist && k < hist_cap) memcpy(d_hist + (size_t)k * (size_t)n, d, sizeof(double) * (size_t)n);
+        if (band_mode == 1) conv = (k + 1) / 2 > i;
         if (conv) i += 1;
         if (i > rho - 1) {
             status = OR_OK;

@@ -41,8 +41,9 @@ class PTPError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("eps_abs", ctypes.c_double), ("max_iter", ctypes.c_int64),
-                ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("trace", ctypes.c_void_p),
-                ("trace_cap", ctypes.c_int64), ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p)]
+                ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("band_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64),
+                ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -89,6 +90,8 @@ def load(path: str | None = None):
             "ptp_distance": (st, [P, P, P, P, P]),
             "ptp_last_stats": (st, [P, P, P]),
             "ptp_distance_noalloc": (st, [P, P, P, P, P]),
+            "ptp_voronoi": (st, [P, P, i32, ctypes.c_int, P, P, P, P, P]),
+            "ptp_fps": (st, [P, i32, i32, P, P, P, ctypes.c_int, P, P]),
             "ptp_geodesic": (st, [P, i64, P, i64, P, i32, ctypes.c_int, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -281,6 +284,33 @@ def ptp_distance_noalloc(tops: Toplesets, params: Params, d_out, stream=None, st
 
 
 PTP_NOALLOC_MAX_VERTS = 1048576
+
+
+def ptp_voronoi(mesh: Mesh, seeds, params: Params, d_out=None, label_out=None, stream=None, stats: bool = True,
+                ok=(PTP_OK,)) -> dict | None:
+    """Multi-source map from `seeds` with the index of the nearest seed per
+    vertex (torch CUDA tensors: d_out float32 [n], label_out int32 [n])."""
+    ps, ks, keep = _array_arg(seeds, np.int32)
+    st = Stats() if stats else None
+    code = load().ptp_voronoi(mesh.handle, ps, int(np.prod(keep.shape)), ks, ctypes.byref(params),
+                              ctypes.c_void_p(d_out.data_ptr()) if d_out is not None else None,
+                              ctypes.c_void_p(label_out.data_ptr()) if label_out is not None else None,
+                              _stream_ptr(stream), ctypes.byref(st) if st is not None else None)
+    _check(code, "ptp_voronoi", ok)
+    return st.as_dict() if st is not None else None
+
+
+def ptp_fps(mesh: Mesh, first: int, n_samples: int, params: Params, samples_out, d_out=None, use_graph: bool = True,
+            stream=None, stats: bool = True, ok=(PTP_OK,)) -> dict | None:
+    """Farthest-point sampling on the device (samples_out: int32 CUDA tensor
+    [n_samples]; d_out: optional float32 CUDA tensor [n])."""
+    st = Stats() if stats else None
+    code = load().ptp_fps(mesh.handle, int(first), int(n_samples), ctypes.byref(params),
+                          ctypes.c_void_p(samples_out.data_ptr()),
+                          ctypes.c_void_p(d_out.data_ptr()) if d_out is not None else None, 1 if use_graph else 0,
+                          _stream_ptr(stream), ctypes.byref(st) if st is not None else None)
+    _check(code, "ptp_fps", ok)
+    return st.as_dict() if st is not None else None
 
 
 def ptp_last_stats(tops: Toplesets, stream=None) -> dict:

@@ -56,6 +56,10 @@ struct DistArgs {
     double eps;
     double eps_abs;
     long long max_iter;
+    const int *perm;  // band position -> vertex, when the data stay in the original order
+    int *lab0;        // Voronoi labels, double-buffered like d (optional)
+    int *lab1;
+    int band_mode;    // 0: Eq. lower_band; 1: fixed band, i_k = ceil(k / 2)
 };
 
 __device__ __forceinline__ float fsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
@@ -167,10 +171,13 @@ __device__ __noinline__ float tri_update_degenerate(const DistArgs &a, int u, in
 // its fan.  The geometry was loaded with the ring (one round trip); here
 // only the neighbours' distances are gathered (the second).  Triangles whose
 // two neighbours are both no closer than the current best are skipped: the
-// update never returns less than min(d1, d2).
+// update never returns less than min(d1, d2).  With LABELS the new value
+// carries the label of the winning triangle's closer neighbour (Voronoi
+// regions, Sec. 4.3).
+template <bool LABELS>
 __device__ __forceinline__ float update_ring(const DistArgs &a, int u, const int ids[PTP_RING], const float el[PTP_RING],
                                              const float4 g[PTP_TRI], int m, float best, const float *__restrict__ dp,
-                                             unsigned &nfp64) {
+                                             const int *__restrict__ lp, int &label, unsigned &nfp64) {
     float dn[PTP_RING];
 #pragma unroll
     for (int t = 0; t < PTP_RING; ++t) dn[t] = t < m ? __ldcg(dp + ids[t]) : INF;
@@ -184,7 +191,10 @@ __device__ __forceinline__ float update_ring(const DistArgs &a, int u, const int
                 ++nfp64;
                 c = tri_update_degenerate(a, u, ids[t], ids[t + 1], dn[t], dn[t + 1], el[t], el[t + 1]);
             }
-            best = fminf(best, c);
+            if (c < best) {
+                best = c;
+                if (LABELS) label = __ldcg(lp + (dn[t] <= dn[t + 1] ? ids[t] : ids[t + 1]));
+            }
         }
     }
     return best;
@@ -192,7 +202,7 @@ __device__ __forceinline__ float update_ring(const DistArgs &a, int u, const int
 
 // New value of a GENERAL vertex from its corner list.
 __device__ __noinline__ float update_general(const DistArgs &a, int u, float best, const float *__restrict__ dp,
-                                             unsigned &nfp64) {
+                                             const int *__restrict__ lp, int *label, unsigned &nfp64) {
     const float3 x0 = xyz(__ldg(a.pos + u));
     const int cb = __ldg(a.row + u), ce = __ldg(a.row + u + 1);
     for (int c = cb; c < ce; ++c) {
@@ -201,7 +211,11 @@ __device__ __noinline__ float update_general(const DistArgs &a, int u, float bes
         if (!(fminf(d1, d2) < best)) continue;
         const float3 e1 = sub3(xyz(__ldg(a.pos + pr.x)), x0), e2 = sub3(xyz(__ldg(a.pos + pr.y)), x0);
         const float a1 = dot3(e1, e1), a2 = dot3(e2, e2);
-        best = fminf(best, tri_update(e1, e2, d1, d2, a1, fsqrt(a1), a2, fsqrt(a2), nfp64));
+        const float cand = tri_update(e1, e2, d1, d2, a1, fsqrt(a1), a2, fsqrt(a2), nfp64);
+        if (cand < best) {
+            best = cand;
+            if (label) *label = __ldcg(lp + (d1 <= d2 ? pr.x : pr.y));
+        }
     }
     return best;
 }
@@ -245,15 +259,20 @@ struct Band {
 };
 
 // The persistent window kernel.  Each iteration walks the band in chunks of
-// 32 consecutive renumbered vertices (coalesced), chunk c to warp c mod W
-// with the warps numbered across CTAs first, so even a narrow band spreads
-// over all SMs.  Pass 1 reads each vertex's own distance and change stamps
-// and queues, in shared memory, the vertices some neighbour of which
-// changed in the previous iteration; pass 2 recomputes the queued vertices
-// with every lane busy.  Long bands are handled in rounds that fit the
-// queue.  The next iteration's band bounds are fetched before the barrier,
-// so after it only distances written in this iteration are on the critical
-// path.
+// 32 consecutive band positions (coalesced), chunk c to warp c mod W with
+// the warps numbered across CTAs first, so even a narrow band spreads over
+// all SMs.  Pass 1 reads each vertex's own distance and change stamps and
+// queues, in shared memory, the vertices some neighbour of which changed in
+// the previous iteration; pass 2 recomputes the queued vertices with every
+// lane busy.  Long bands are handled in rounds that fit the queue.  The next
+// iteration's band bounds are fetched before the barrier, so after it only
+// distances written in this iteration are on the critical path.
+//
+// PERM: the vertex data stay in the original order and band position p holds
+// vertex perm[p] (multi-source maps, where the paper also skips the
+// rearrangement, Sec. 4.1); otherwise position p is vertex p of the
+// renumbered mesh.  LABELS: also carry a label per vertex (Voronoi regions).
+template <bool PERM, bool LABELS>
 __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(DistArgs a) {
     const int rho = __ldcg(a.info);
     const int nsrc = __ldcg(a.off + 1);
@@ -272,10 +291,11 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     __shared__ float s_max[DIST_THREADS / 32];
     __shared__ double s_sum[DIST_THREADS / 32];
     __shared__ int s_cnt[2][DIST_THREADS / 32];
-    __shared__ int2 s_queue[QUEUE_CAP];  // (vertex, bits of d_{k-1})
+    __shared__ int2 s_queue[QUEUE_CAP];  // (vertex | in V_i << 31, bits of d_{k-1})
     __shared__ int s_nq;
 
     auto off_at = [&](int r) { return __ldcg(a.off + (r < rho ? r : rho)); };
+    auto vertex_at = [&](int pos) { return PERM ? __ldg(a.perm + pos) : pos; };
     Band bd;  // iteration 1: i_0 = 0, j_1 = min(1, rho - 1)
     {
         const int j1 = rho > 1 ? 1 : 0;
@@ -290,6 +310,8 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         const int j = k < rho ? (int)k : rho - 1;
         const float *dp = (k & 1) ? a.d0 : a.d1;  // d_{k-1} lives in buffer (k-1) % 2
         float *dnx = (k & 1) ? a.d1 : a.d0;
+        const int *lp = (k & 1) ? a.lab0 : a.lab1;
+        int *lnx = (k & 1) ? a.lab1 : a.lab0;
         const bool entering = (long long)j == k;
         const int first = bd.lo > nsrc ? bd.lo : nsrc;
         const int start = bd.copy_lo < first ? bd.copy_lo : first;
@@ -309,29 +331,42 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             // pass 1: state of each band vertex; queue the ones to recompute.
             // The state of P1_BATCH chunks is loaded before any is used.
             for (int m = m0; m < m0 + ROUND_CHUNKS && m < rounds_m; m += P1_BATCH) {
-                int uu[P1_BATCH], ns[P1_BATCH], cg[P1_BATCH];
+                int pp[P1_BATCH], uu[P1_BATCH], ns[P1_BATCH], cg[P1_BATCH];
                 float dold[P1_BATCH];
                 bool live[P1_BATCH];
 #pragma unroll
                 for (int q = 0; q < P1_BATCH; ++q) {
-                    uu[q] = base + (gwarp + (m + q) * nwarps) * 32 + lane;
-                    const bool ok = m + q < rounds_m && uu[q] >= start && uu[q] < bd.hi && uu[q] >= nsrc;
-                    live[q] = ok && uu[q] >= bd.lo;
-                    dold[q] = ok ? __ldcg(dp + uu[q]) : 0.0f;
-                    ns[q] = live[q] ? __ldcg(a.nstamp + uu[q]) : -2;
-                    cg[q] = live[q] ? __ldcg(a.chg + uu[q]) : -2;
-                    if (ok && !live[q]) dnx[uu[q]] = dold[q];  // retired after the previous iteration
+                    pp[q] = base + (gwarp + (m + q) * nwarps) * 32 + lane;
+                    const bool ok = m + q < rounds_m && pp[q] >= start && pp[q] < bd.hi && pp[q] >= nsrc;
+                    live[q] = ok && pp[q] >= bd.lo;
+                    uu[q] = ok ? vertex_at(pp[q]) : 0;
                 }
 #pragma unroll
                 for (int q = 0; q < P1_BATCH; ++q) {
-                    const bool need = live[q] && ((entering && uu[q] >= bd.vj_beg) || ns[q] >= k - 1);
-                    if (live[q] && !need && cg[q] == k - 1) dnx[uu[q]] = dold[q];
+                    const bool ok = m + q < rounds_m && pp[q] >= start && pp[q] < bd.hi && pp[q] >= nsrc;
+                    dold[q] = ok ? __ldcg(dp + uu[q]) : 0.0f;
+                    ns[q] = live[q] ? __ldcg(a.nstamp + uu[q]) : -2;
+                    cg[q] = live[q] ? __ldcg(a.chg + uu[q]) : -2;
+                    if (ok && !live[q]) {  // retired after the previous iteration
+                        dnx[uu[q]] = dold[q];
+                        if (LABELS) lnx[uu[q]] = __ldcg(lp + uu[q]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < P1_BATCH; ++q) {
+                    const bool need = live[q] && ((entering && pp[q] >= bd.vj_beg) || ns[q] >= k - 1);
+                    if (live[q] && !need && cg[q] == k - 1) {
+                        dnx[uu[q]] = dold[q];
+                        if (LABELS) lnx[uu[q]] = __ldcg(lp + uu[q]);
+                    }
                     const unsigned bal = __ballot_sync(0xffffffffu, need);
                     if (bal) {
                         int at = 0;
                         if (lane == 0) at = atomicAdd(&s_nq, __popc(bal));
                         at = __shfl_sync(0xffffffffu, at, 0);
-                        if (need) s_queue[at + __popc(bal & ((1u << lane) - 1u))] = make_int2(uu[q], __float_as_int(dold[q]));
+                        if (need)
+                            s_queue[at + __popc(bal & ((1u << lane) - 1u))] =
+                                make_int2(uu[q] | (pp[q] < bd.vi_end ? (int)0x80000000 : 0), __float_as_int(dold[q]));
                     }
                 }
             }
@@ -340,7 +375,8 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             const int nq = s_nq;
             for (int q = threadIdx.x; q < nq; q += blockDim.x) {
                 const int2 ent = s_queue[q];
-                const int u = ent.x;
+                const int u = ent.x & 0x7fffffff;
+                const bool in_vi = ent.x < 0;
                 const float dold = __int_as_float(ent.y);
                 const int meta = __ldg(a.meta + u);
                 const int4 r0 = __ldg(a.ring + u), r1 = __ldg(a.ring + a.n + u);
@@ -352,11 +388,13 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                     g[t] = t < m - 1 ? __ldg(a.tgeom + (size_t)t * a.n + u) : make_float4(0.f, 0.f, 0.f, 0.f);
                 const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
                 const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+                int label = LABELS ? __ldcg(lp + u) : 0;
                 float dnew;
-                if (meta & PTP_META_GENERAL) dnew = update_general(a, u, dold, dp, nfp64);
-                else dnew = update_ring(a, u, ids, el, g, m, dold, dp, nfp64);
+                if (meta & PTP_META_GENERAL) dnew = update_general(a, u, dold, dp, lp, LABELS ? &label : nullptr, nfp64);
+                else dnew = update_ring<LABELS>(a, u, ids, el, g, m, dold, dp, lp, label, nfp64);
                 ++n_active;
                 dnx[u] = dnew;
+                if (LABELS) lnx[u] = label;
                 if (dnew != dold) {
                     ++n_changed;
                     a.chg[u] = (int)k;
@@ -368,7 +406,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                         for (int t = 0; t < PTP_RING; ++t)
                             if (t < cnt) a.nstamp[ids[t]] = (int)k;
                     }
-                    if (u < bd.vi_end) {
+                    if (in_vi) {
                         // relative-change test of Eq. lower_band, in FP64 (the
                         // difference of two floats is exact in double)
                         const double o = dold, delta = o - (double)dnew;
@@ -390,7 +428,6 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             const float wm = warp_max_f(maxrel);
             const double ws = warp_sum_d(errsum);
             const int wa = warp_sum_i(n_active), wc = warp_sum_i(n_changed);
-            const int wid = threadIdx.x >> 5;
             if (lane == 0) {
                 s_max[wid] = wm;
                 s_sum[wid] = ws;
@@ -427,18 +464,20 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             status = PTP_ERR_TIMEOUT;
             break;
         }
+        // Eq. lower_band, or the fixed band whose lower bound is ceil(k / 2)
+        const bool advance = a.band_mode == 1 ? (int)((k + 1) >> 1) > i : failed == 0;
         if (leader) {
             band_updates += bd.hi - first;
             if (a.trace && k - 1 < a.trace_cap) {
                 ptp_trace_rec *rec = a.trace + (k - 1);
                 rec->i = i;
                 rec->j = j;
-                rec->advanced = failed ? 0 : 1;
+                rec->advanced = advance ? 1 : 0;
             }
         }
-        if (!failed) {
-            // Eq. lower_band: i_k = i_{k-1} + 1; V_{i_{k-1}} retires and is
-            // copied forward in the next iteration (V_0 never changes)
+        if (advance) {
+            // i_k = i_{k-1} + 1: V_{i_{k-1}} retires and is copied forward in
+            // the next iteration (V_0 never changes)
             ++i;
             if (i > rho - 1) {
                 status = PTP_OK;
@@ -494,6 +533,36 @@ __global__ void scatter_out(const int *__restrict__ perm, int n, const float *__
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) out[perm[u]] = d[u];
 }
 
+// Multi-source runs in the original order: distances +inf and labels
+// "none" everywhere, then the sources.
+__global__ void init_multi(int n, float *__restrict__ d0, float *__restrict__ d1, int *__restrict__ nstamp,
+                           int *__restrict__ chg, int *__restrict__ lab0, int *__restrict__ lab1) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        d0[u] = INF;
+        d1[u] = INF;
+        nstamp[u] = -2;
+        chg[u] = -2;
+        if (lab0) {
+            lab0[u] = 0x7fffffff;
+            lab1[u] = 0x7fffffff;
+        }
+    }
+}
+
+__global__ void seed_multi(const int *__restrict__ src, int m, const int *__restrict__ m_dev, float *__restrict__ d0,
+                           float *__restrict__ d1, int *__restrict__ lab0, int *__restrict__ lab1) {
+    if (m_dev) m = *m_dev;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < m; q += gridDim.x * blockDim.x) {
+        const int v = src[q];
+        d0[v] = 0.0f;
+        d1[v] = 0.0f;
+        if (lab0) {
+            atomicMin(&lab0[v], q);  // a repeated seed keeps its first index
+            atomicMin(&lab1[v], q);
+        }
+    }
+}
+
 unsigned blocks_for(int64_t work, int threads, int device) {
     int64_t b = (work + threads - 1) / threads;
     const int64_t cap = (int64_t)ptp_num_sms(device) * 16;
@@ -503,6 +572,56 @@ unsigned blocks_for(int64_t work, int threads, int device) {
 }
 
 }  // namespace
+
+ptp_status ptp_internal_window_multi(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params,
+                                     const int *src, const int *m_dev, int m_max, bool labels, cudaStream_t s) {
+    const int n = b->n;
+    const int dev = mesh->device;
+    PTP_TRY(cudaMemsetAsync(b->ctrl, 0, sizeof(ptp_ctrl), s));
+    init_multi<<<blocks_for(n, 256, dev), 256, 0, s>>>(n, b->d0, b->d1, b->nstamp, b->chg, labels ? b->lab0 : nullptr,
+                                                        labels ? b->lab1 : nullptr);
+    seed_multi<<<blocks_for(m_max, 256, dev), 256, 0, s>>>(src, m_max, m_dev, b->d0, b->d1, labels ? b->lab0 : nullptr,
+                                                           labels ? b->lab1 : nullptr);
+    ptp_count_launches(2);
+    PTP_TRY(cudaGetLastError());
+    const void *fn = labels ? (const void *)ptp_window<true, true> : (const void *)ptp_window<true, false>;
+    int per_sm = 0;
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, DIST_THREADS, 0));
+    if (per_sm < 1) return PTP_ERR_CUDA;
+    int grid = per_sm * ptp_num_sms(dev);
+    if (params->grid > 0 && params->grid < grid) grid = params->grid;
+    DistArgs a;
+    a.n = n;
+    a.pos = mesh->pos;
+    a.ring = mesh->ring;
+    a.tgeom = mesh->tgeom;
+    a.elen = mesh->elen;
+    a.meta = mesh->meta;
+    a.row = mesh->row;
+    a.pairs = mesh->pairs;
+    a.off = b->off;
+    a.info = b->info;
+    a.d0 = b->d0;
+    a.d1 = b->d1;
+    a.nstamp = b->nstamp;
+    a.chg = b->chg;
+    a.ctrl = b->ctrl;
+    a.trace = (ptp_trace_rec *)params->trace;
+    a.trace_cap = params->trace ? params->trace_cap : 0;
+    a.eps = params->eps;
+    a.eps_abs = params->eps_abs;
+    a.max_iter = params->max_iter;
+    a.perm = b->queue;
+    a.lab0 = labels ? b->lab0 : nullptr;
+    a.lab1 = labels ? b->lab1 : nullptr;
+    a.band_mode = params->band_mode;
+    if (params->trace && params->trace_cap > 0)
+        PTP_TRY(cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s));
+    void *args[] = {(void *)&a};
+    PTP_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(DIST_THREADS), args, 0, s));
+    ptp_count_launches(1);
+    return PTP_OK;
+}
 
 extern "C" ptp_status ptp_last_stats(ptp_toplesets_t *t, void *stream, ptp_stats *st) {
     if (!t || !st) return PTP_ERR_ARG;
@@ -528,6 +647,7 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
     if (!(params->eps >= 0.0) || !(params->eps_abs >= 0.0) || params->max_iter < 0 || params->trace_cap < 0)
         return PTP_ERR_ARG;
     if (params->block != 0 && params->block != DIST_THREADS) return PTP_ERR_ARG;
+    if (params->band_mode != 0 && params->band_mode != 1) return PTP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = t->n;
     const int dev = t->device;
@@ -554,7 +674,7 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
         if (ce != cudaSuccess) break;
 
         int per_sm = 0;
-        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window, DIST_THREADS, 0);
+        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false>, DIST_THREADS, 0);
         if (ce != cudaSuccess) break;
         if (per_sm < 1) { st = PTP_ERR_CUDA; break; }
         int grid = per_sm * ptp_num_sms(dev);
@@ -581,12 +701,15 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
         a.eps = params->eps;
         a.eps_abs = params->eps_abs;
         a.max_iter = params->max_iter;
+        a.perm = nullptr;
+        a.lab0 = a.lab1 = nullptr;
+        a.band_mode = params->band_mode;
         void *args[] = {(void *)&a};
         if (params->ev_begin) {
             ce = cudaEventRecord((cudaEvent_t)params->ev_begin, s);
             if (ce != cudaSuccess) break;
         }
-        ce = cudaLaunchCooperativeKernel((const void *)ptp_window, dim3(grid), dim3(DIST_THREADS), args, 0, s);
+        ce = cudaLaunchCooperativeKernel((const void *)ptp_window<false, false>, dim3(grid), dim3(DIST_THREADS), args, 0, s);
         if (ce != cudaSuccess) break;
         ptp_count_launches(1);
         if (params->ev_end) {
@@ -681,6 +804,7 @@ extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params 
     if (!(params->eps >= 0.0) || !(params->eps_abs >= 0.0) || params->max_iter < 0 || params->trace_cap < 0)
         return PTP_ERR_ARG;
     if (params->block != 0 && params->block != DIST_THREADS) return PTP_ERR_ARG;
+    if (params->band_mode != 0 && params->band_mode != 1) return PTP_ERR_ARG;
     if (t->n > (int64_t)PTP_NOALLOC_MAX_VERTS) return PTP_ERR_TOO_LARGE;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = t->n;
@@ -702,7 +826,7 @@ extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params 
     ptp_count_launches(1);
     PTP_TRY(cudaGetLastError());
     int per_sm = 0;
-    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window, DIST_THREADS, 0));
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false>, DIST_THREADS, 0));
     if (per_sm < 1) return PTP_ERR_CUDA;
     int grid = per_sm * ptp_num_sms(dev);
     if (params->grid > 0 && params->grid < grid) grid = params->grid;
@@ -728,9 +852,12 @@ extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params 
     a.eps = params->eps;
     a.eps_abs = params->eps_abs;
     a.max_iter = params->max_iter;
+    a.perm = nullptr;
+    a.lab0 = a.lab1 = nullptr;
+    a.band_mode = params->band_mode;
     void *args[] = {(void *)&a};
     if (params->ev_begin) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_begin, s));
-    PTP_TRY(cudaLaunchCooperativeKernel((const void *)ptp_window, dim3(grid), dim3(DIST_THREADS), args, 0, s));
+    PTP_TRY(cudaLaunchCooperativeKernel((const void *)ptp_window<false, false>, dim3(grid), dim3(DIST_THREADS), args, 0, s));
     ptp_count_launches(1);
     if (params->ev_end) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_end, s));
     scatter_out<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, dbuf, dbuf + n, ctrl, d_out);

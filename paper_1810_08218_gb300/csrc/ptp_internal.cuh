@@ -35,6 +35,8 @@ struct ptp_mesh {
                           //        in the face's cyclic order
     int4 *ring;           // [2 n] one-ring slots, original numbering (layout below)
     int *meta;            // [n]
+    float4 *tgeom;        // ring geometry in the original numbering, built on the
+    float4 *elen;         //   first multi-source call (NULL until then)
     double diameter;      // bounding-box diagonal
 };
 
@@ -94,9 +96,40 @@ struct ptp_toplesets_s {
     ptp_ctrl *ctrl;  // control block of the last ptp_distance run
 };
 
+// Scratch of one multi-source run in the original vertex order (Voronoi, FPS).
+struct ptp_multi_bufs {
+    int n;
+    int *level;                 // [n]
+    int *queue;                 // [n] BFS queue: band position -> vertex
+    int *off;                   // [n + 2]
+    int *info;                  // [4]
+    int *spill;                 // [2 n]
+    int *cnt;                   // [16] BFS counters
+    float *d0, *d1;             // [n] each
+    int *nstamp, *chg;          // [n] each
+    int *lab0, *lab1;           // [n] each, or NULL without labels
+    ptp_ctrl *ctrl;
+};
+
 // ---------------------------------------------------------------------------
 // Helpers shared by the translation units (host side)
 // ---------------------------------------------------------------------------
+
+// One-off kernel attributes (the BFS cluster kernel's shared memory); call
+// before any stream capture.
+ptp_status ptp_internal_prepare();
+// Toplesets of the sources src[0 .. *m_dev) into b->level / queue / off / info
+// (BFS queue order, no renumbering).  Resets the per-run BFS state itself.
+ptp_status ptp_internal_bfs(const ptp_mesh *mesh, ptp_multi_bufs *b, const int *src, const int *m_dev, int m_max,
+                            cudaStream_t s);
+// Ring geometry of the mesh in the original numbering (cached in the mesh).
+ptp_status ptp_internal_mesh_geometry(ptp_mesh *mesh, cudaStream_t s);
+// Initialise distances (0 on the sources, which get labels 0..m-1) and run
+// the window kernel over b->queue in the original order.
+ptp_status ptp_internal_window_multi(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params,
+                                     const int *src, const int *m_dev, int m_max, bool labels, cudaStream_t s);
+// The final distance (and label) buffer of the last window run in b.
+__host__ __device__ inline int ptp_final_buffer(long long iterations) { return (int)(iterations & 1); }
 
 int ptp_num_sms(int device);
 

@@ -37,6 +37,8 @@ extern "C" ptp_status ptp_params_default(ptp_params *p) {
     p->max_iter = 0;
     p->block = 0;
     p->grid = 0;
+    p->band_mode = 0;
+    p->reserved = 0;
     p->trace = nullptr;
     p->trace_cap = 0;
     p->ev_begin = nullptr;
@@ -46,7 +48,7 @@ extern "C" ptp_status ptp_params_default(ptp_params *p) {
 
 static unsigned long long g_launches = 0;
 
-void ptp_count_launches(int n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+void ptp_count_launches(int n) { __atomic_fetch_add(&g_launches, (unsigned long long)(long long)n, __ATOMIC_RELAXED); }
 
 extern "C" int64_t ptp_kernel_launches(void) { return (int64_t)__atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
@@ -456,6 +458,8 @@ extern "C" ptp_status ptp_mesh_destroy(ptp_mesh *m) {
     cudaFreeAsync(m->pairs, m->stream);
     cudaFreeAsync(m->ring, m->stream);
     cudaFreeAsync(m->meta, m->stream);
+    if (m->tgeom) cudaFreeAsync(m->tgeom, m->stream);
+    if (m->elen) cudaFreeAsync(m->elen, m->stream);
     const cudaError_t e = cudaStreamSynchronize(m->stream);
     free(m);
     return e == cudaSuccess ? PTP_OK : ptp_internal_cuda_status(e);

@@ -21,8 +21,11 @@ constexpr int BC_CLUSTER = 8;     // CTAs in the BFS cluster (portable maximum)
 constexpr int BC_THREADS = 1024;  // threads per CTA
 constexpr int BC_CAP = 12288;     // frontier entries per CTA list (two lists: 96 KiB)
 
-__global__ void bfs_seed(const int *__restrict__ src, int m, int *__restrict__ level, int *__restrict__ queue,
-                         int *__restrict__ info) {
+// V_0: claim the sources (duplicates once).  The count is m, or *m_dev when
+// m_dev is given (device-side source lists, e.g. farthest-point sampling).
+__global__ void bfs_seed(const int *__restrict__ src, int m, const int *__restrict__ m_dev, int *__restrict__ level,
+                         int *__restrict__ queue, int *__restrict__ info) {
+    if (m_dev) m = *m_dev;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < m; s += gridDim.x * blockDim.x) {
         const int v = src[s];
         if (atomicCAS(&level[v], -1, 0) == -1) queue[atomicAdd(&info[3], 1)] = v;
@@ -319,6 +322,49 @@ unsigned blocks_for(int64_t work, int threads, int device) {
 
 }  // namespace
 
+ptp_status ptp_internal_prepare() {
+    PTP_TRY(cudaFuncSetAttribute(bfs_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(int) * 2 * BC_CAP)));
+    return PTP_OK;
+}
+
+ptp_status ptp_internal_bfs(const ptp_mesh *mesh, ptp_multi_bufs *b, const int *src, const int *m_dev, int m_max,
+                            cudaStream_t s) {
+    const int n = b->n;
+    PTP_TRY(cudaMemsetAsync(b->level, 0xFF, sizeof(int) * n, s));
+    PTP_TRY(cudaMemsetAsync(b->info, 0, sizeof(int) * 4, s));
+    PTP_TRY(cudaMemsetAsync(b->cnt, 0, sizeof(int) * 16, s));
+    bfs_seed<<<blocks_for(m_max, 256, mesh->device), 256, 0, s>>>(src, m_max, m_dev, b->level, b->queue, b->info);
+    bfs_cluster<<<BC_CLUSTER, BC_THREADS, sizeof(int) * 2 * BC_CAP, s>>>(mesh->ring, mesh->meta, mesh->row, mesh->pairs,
+                                                                         n, b->level, b->queue, b->off, b->info, b->spill,
+                                                                         b->cnt);
+    ptp_count_launches(2);
+    PTP_TRY(cudaGetLastError());
+    return PTP_OK;
+}
+
+ptp_status ptp_internal_mesh_geometry(ptp_mesh *mesh, cudaStream_t s) {
+    if (mesh->tgeom) return PTP_OK;
+    const int64_t n = mesh->n;
+    float4 *tg = nullptr, *el = nullptr;
+    PTP_TRY(cudaMallocAsync((void **)&tg, sizeof(float4) * PTP_TRI * n, s));
+    cudaError_t e = cudaMallocAsync((void **)&el, sizeof(float4) * 2 * n, s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(tg, s);
+        return ptp_internal_cuda_status(e);
+    }
+    build_geometry<<<blocks_for(n, 128, mesh->device), 128, 0, s>>>((int)n, mesh->pos, mesh->ring, mesh->meta, tg, el);
+    ptp_count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFreeAsync(tg, s);
+        cudaFreeAsync(el, s);
+        return ptp_internal_cuda_status(e);
+    }
+    mesh->tgeom = tg;
+    mesh->elen = el;
+    return PTP_OK;
+}
+
 extern "C" ptp_status ptp_toplesets(ptp_mesh *mesh, const int32_t *sources, int32_t m, int ptr_kind, void *stream,
                                     ptp_toplesets_t **out) {
     if (!out) return PTP_ERR_ARG;
@@ -386,12 +432,13 @@ extern "C" ptp_status ptp_toplesets(ptp_mesh *mesh, const int32_t *sources, int3
         TOPS_TRY(cudaMemsetAsync(t->off, 0, sizeof(int) * (n + 2), s));
         TOPS_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * 16, s));
         TOPS_TRY(cudaMemsetAsync(t->ctrl, 0, sizeof(ptp_ctrl), s));
-        bfs_seed<<<blocks_for(m, 256, dev), 256, 0, s>>>(src_d, m, t->level, t->perm, t->info);
+        bfs_seed<<<blocks_for(m, 256, dev), 256, 0, s>>>(src_d, m, nullptr, t->level, t->perm, t->info);
         ptp_count_launches(1);
         TOPS_TRY(cudaGetLastError());
         {
             const size_t smem = sizeof(int) * 2 * BC_CAP;
-            TOPS_TRY(cudaFuncSetAttribute(bfs_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            st = ptp_internal_prepare();
+            if (st != PTP_OK) goto fail;
             bfs_cluster<<<BC_CLUSTER, BC_THREADS, smem, s>>>(mesh->ring, mesh->meta, mesh->row, mesh->pairs, (int)n,
                                                              t->level, t->perm, t->off, t->info, spill, cnt);
             ptp_count_launches(1);

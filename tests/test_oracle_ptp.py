@@ -181,3 +181,16 @@ def test_not_converged_cap():
     level, _ = oracle.toplesets(V.shape[0], F, S)
     # after 10 iterations exactly the toplesets V_0 .. V_10 carry finite values
     assert np.array_equal(np.isfinite(r.d), level <= 10)
+
+
+def test_fixed_band_variant_follows_its_rule():
+    """band_mode 1 (the fixed band of the complexity analysis, Sec. 5): the
+    lower bound after iteration k is ceil(k/2) regardless of convergence, so
+    the run takes 2*rho - 1 iterations and still reaches the Dijkstra-bounded
+    distances."""
+    V, F, S = meshes.flat65()
+    r = oracle.ptp(V, F, S, band_mode=1, trace=True)
+    assert r.K == 2 * r.rho - 1
+    assert np.array_equal(r.trace_i, [(k - 1 + 1) // 2 for k in range(1, r.K + 1)])
+    ex = np.linalg.norm(V - V[S[0]], axis=1)
+    assert _mape(r.d, ex) < 2.5
