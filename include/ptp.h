@@ -78,6 +78,12 @@ typedef struct ptp_params {
     void *ev_begin;    /* optional cudaEvent_t recorded on `stream` right before the
                           window kernel, or NULL                                   */
     void *ev_end;      /* optional cudaEvent_t recorded right after it, or NULL     */
+    const int32_t *schedule; /* optional DEVICE array [rho]: for each topleset i,
+                          the number of iterations the band's lower bound is
+                          expected to stay at i (a learned schedule, see
+                          ptp_mlp_infer).  The test of Eq. lower_band is skipped
+                          until that many iterations have passed, then applied
+                          as usual every iteration.  NULL: test every iteration */
 } ptp_params;
 
 /* One record per PTP iteration k (written only when params.trace is set). */
@@ -99,6 +105,7 @@ typedef struct ptp_stats {
     int64_t fp64_solves;     /* triangle solves taken in FP64 (near-degenerate)     */
     int32_t rho;             /* number of toplesets                                 */
     int32_t status;          /* ptp_status of the device-side run                   */
+    int64_t checks;          /* iterations that applied the test of Eq. lower_band  */
 } ptp_stats;
 
 /* Human-readable name of a status code (static storage). */
@@ -245,6 +252,47 @@ ptp_status ptp_voronoi(ptp_mesh *mesh, const int32_t *seeds, int32_t m, int ptr_
  */
 ptp_status ptp_fps(ptp_mesh *mesh, int32_t first, int32_t n_samples, const ptp_params *params, int32_t *samples_out,
                    float *d_out, int use_graph, void *stream, ptp_stats *stats);
+
+/*
+ * Learned iteration schedule (an extension of the method; the paper has no
+ * counterpart).  A multilayer perceptron 6 -> 32 -> 32 -> 1 (ReLU) with FP16
+ * weights and FP32 accumulation predicts, per topleset window, log2 of the
+ * number of iterations the band's lower bound stays at that topleset.
+ * Parameters: PTP_MLP_NPARAM values, flat, in the order W1[32][6], b1[32],
+ * W2[32][32], b2[32], W3[32], b3 (FP32 master copy; FP16 copy as IEEE
+ * binary16 bit patterns).
+ */
+#define PTP_MLP_NPARAM 1313
+#define PTP_WINDOW_FEATURES 6
+
+/* Per-topleset window features [rho][6] (DEVICE float32): log2(|V_r|+1)/20,
+ * ring-edge length mean and std over V_r relative to the mesh mean, the
+ * smallest triangle angle at V_r's vertices, std/mean of the Euclidean
+ * distance from the first source over V_r (how far the topleset is from a
+ * sphere around the source, i.e. from the distance isocurves, which the paper
+ * ties to the iteration count, Sec. 4.2), and r / rho.  feat_out must hold
+ * 6 * n_verts floats.  Asynchronous. */
+ptp_status ptp_window_features(ptp_toplesets_t *tops, float *feat_out, void *stream);
+
+/* Schedule from features: sched_out[s] = clamp(floor(2^(y_s - margin)), 1,
+ * cap) for s < count (or < *count_dev when count_dev is non-NULL, a DEVICE
+ * int32, e.g. &info[0] = rho).  All arrays DEVICE.  Asynchronous. */
+ptp_status ptp_mlp_infer(const uint16_t *w_half, const float *feat, int32_t count, const int32_t *count_dev,
+                         float margin, int32_t cap, int32_t *sched_out, void *stream);
+
+/* One fused forward + backward pass over `count` samples (X [count][6],
+ * targets Y [count], DEVICE): adds d(loss)/d(params) to grad [PTP_MLP_NPARAM]
+ * and the loss sum((y - t)^2) / count to *loss (if non-NULL).  Asynchronous. */
+ptp_status ptp_mlp_grad(const uint16_t *w_half, const float *X, const float *Y, int32_t count, float *grad,
+                        float *loss, void *stream);
+
+/* Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step >= 1) on the FP32 master
+ * weights with moments m, v; refreshes w_half and zeroes grad.  DEVICE. */
+ptp_status ptp_mlp_adam(float *w_master, uint16_t *w_half, float *m, float *v, float *grad, float lr, int32_t step,
+                        void *stream);
+
+/* FP32 parameters -> FP16 copy.  DEVICE. */
+ptp_status ptp_mlp_to_half(const float *w, uint16_t *w_half, void *stream);
 
 /* Statistics of the last ptp_distance call on this handle.  Blocks on
  * `stream`.  Returns that call's device-side status. */

@@ -43,13 +43,13 @@ class Params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("eps_abs", ctypes.c_double), ("max_iter", ctypes.c_int64),
                 ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("band_mode", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64),
-                ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p)]
+                ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p), ("schedule", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("band_updates", ctypes.c_int64), ("active_updates", ctypes.c_int64),
                 ("changed", ctypes.c_int64), ("fp64_solves", ctypes.c_int64), ("rho", ctypes.c_int32),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("checks", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -91,6 +91,11 @@ def load(path: str | None = None):
             "ptp_last_stats": (st, [P, P, P]),
             "ptp_distance_noalloc": (st, [P, P, P, P, P]),
             "ptp_voronoi": (st, [P, P, i32, ctypes.c_int, P, P, P, P, P]),
+            "ptp_window_features": (st, [P, P, P]),
+            "ptp_mlp_infer": (st, [P, P, i32, P, ctypes.c_float, i32, P, P]),
+            "ptp_mlp_grad": (st, [P, P, P, i32, P, P, P]),
+            "ptp_mlp_adam": (st, [P, P, P, P, P, ctypes.c_float, i32, P]),
+            "ptp_mlp_to_half": (st, [P, P, P]),
             "ptp_fps": (st, [P, i32, i32, P, P, P, ctypes.c_int, P, P]),
             "ptp_geodesic": (st, [P, i64, P, i64, P, i32, ctypes.c_int, P, P, P, P]),
         }
@@ -347,3 +352,41 @@ def ptp_geodesic(xyz, faces, sources, params: Params, d_out, stream=None, ok=(PT
                             ctypes.byref(st))
     _check(code, "ptp_geodesic", ok)
     return st.as_dict()
+
+
+# --------------------------------------------------------------------------
+# learned schedule (MLP kernels)
+# --------------------------------------------------------------------------
+
+PTP_MLP_NPARAM = 1313
+PTP_WINDOW_FEATURES = 6
+
+
+def _dp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def ptp_window_features(tops: Toplesets, feat_out, stream=None) -> None:
+    """feat_out: float32 CUDA tensor with room for 6 * n floats."""
+    _check(load().ptp_window_features(tops.handle, _dp(feat_out), _stream_ptr(stream)), "ptp_window_features")
+
+
+def ptp_mlp_infer(w_half, feat, count: int, sched_out, margin: float = 0.0, cap: int = 1 << 20, count_dev=None,
+                  stream=None) -> None:
+    _check(load().ptp_mlp_infer(_dp(w_half), _dp(feat), int(count), _dp(count_dev), float(margin), int(cap),
+                                _dp(sched_out), _stream_ptr(stream)), "ptp_mlp_infer")
+
+
+def ptp_mlp_grad(w_half, X, Y, count: int, grad, loss=None, stream=None) -> None:
+    _check(load().ptp_mlp_grad(_dp(w_half), _dp(X), _dp(Y), int(count), _dp(grad), _dp(loss), _stream_ptr(stream)),
+           "ptp_mlp_grad")
+
+
+def ptp_mlp_adam(w_master, w_half, m, v, grad, lr: float, step: int, stream=None) -> None:
+    _check(load().ptp_mlp_adam(_dp(w_master), _dp(w_half), _dp(m), _dp(v), _dp(grad), float(lr), int(step),
+                               _stream_ptr(stream)), "ptp_mlp_adam")
+
+
+def ptp_mlp_to_half(w, w_half, stream=None) -> None:
+    _check(load().ptp_mlp_to_half(_dp(w), _dp(w_half), _stream_ptr(stream)), "ptp_mlp_to_half")
+

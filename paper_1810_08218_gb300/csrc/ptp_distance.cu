@@ -60,6 +60,7 @@ struct DistArgs {
     int *lab0;        // Voronoi labels, double-buffered like d (optional)
     int *lab1;
     int band_mode;    // 0: Eq. lower_band; 1: fixed band, i_k = ceil(k / 2)
+    const int *sched; // learned schedule per topleset, or NULL
 };
 
 __device__ __forceinline__ float fsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
@@ -287,6 +288,8 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     long long band_updates = 0;
     int i = 0;  // i_{k-1}
     long long k = 1;
+    long long check_from = 1;  // first iteration that tests V_i (learned schedule)
+    long long checks = 0;
     int status = PTP_ERR_NOT_CONVERGED;
     __shared__ float s_max[DIST_THREADS / 32];
     __shared__ double s_sum[DIST_THREADS / 32];
@@ -315,6 +318,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         const bool entering = (long long)j == k;
         const int first = bd.lo > nsrc ? bd.lo : nsrc;
         const int start = bd.copy_lo < first ? bd.copy_lo : first;
+        const bool testing = k >= check_from;
 
         int notconv = 0, n_active = 0, n_changed = 0;
         float maxrel = 0.0f;
@@ -406,7 +410,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                         for (int t = 0; t < PTP_RING; ++t)
                             if (t < cnt) a.nstamp[ids[t]] = (int)k;
                     }
-                    if (in_vi) {
+                    if (in_vi && testing) {
                         // relative-change test of Eq. lower_band, in FP64 (the
                         // difference of two floats is exact in double)
                         const double o = dold, delta = o - (double)dnew;
@@ -457,6 +461,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         const int jn = k + 1 < rho ? (int)(k + 1) : rho - 1;
         const int o_i2 = off_at(i + 2);
         const int o_jn = off_at(jn), o_jn1 = off_at(jn + 1);
+        const int sched_next = (a.sched && i + 1 < rho) ? __ldcg(a.sched + i + 1) : 1;
 
         const int any = __syncthreads_or(notconv);
         const long long failed = ptp_grid_sync(a.ctrl->bar, k, any ? 1u : 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi);
@@ -464,10 +469,12 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             status = PTP_ERR_TIMEOUT;
             break;
         }
-        // Eq. lower_band, or the fixed band whose lower bound is ceil(k / 2)
-        const bool advance = a.band_mode == 1 ? (int)((k + 1) >> 1) > i : failed == 0;
+        // Eq. lower_band (applied from iteration check_from on), or the fixed
+        // band whose lower bound is ceil(k / 2)
+        const bool advance = a.band_mode == 1 ? (int)((k + 1) >> 1) > i : (testing && failed == 0);
         if (leader) {
             band_updates += bd.hi - first;
+            checks += testing ? 1 : 0;
             if (a.trace && k - 1 < a.trace_cap) {
                 ptp_trace_rec *rec = a.trace + (k - 1);
                 rec->i = i;
@@ -483,6 +490,9 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                 status = PTP_OK;
                 break;
             }
+            // V_i is the new bottom from iteration k + 1 on; with a schedule
+            // its first test comes after the predicted number of iterations
+            check_from = k + (sched_next > 1 ? sched_next : 1);
             bd.copy_lo = i >= 2 ? bd.lo : bd.vi_end;
             bd.lo = bd.vi_end;
             bd.vi_end = o_i2;
@@ -510,6 +520,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     if (leader) {
         a.ctrl->iterations = k;
         a.ctrl->band_updates = band_updates;
+        a.ctrl->checks = checks;
         if (status != PTP_ERR_TIMEOUT) atomicCAS(&a.ctrl->status, 0, status);
     }
 }
@@ -615,6 +626,7 @@ ptp_status ptp_internal_window_multi(const ptp_mesh *mesh, ptp_multi_bufs *b, co
     a.lab0 = labels ? b->lab0 : nullptr;
     a.lab1 = labels ? b->lab1 : nullptr;
     a.band_mode = params->band_mode;
+    a.sched = params->schedule;
     if (params->trace && params->trace_cap > 0)
         PTP_TRY(cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s));
     void *args[] = {(void *)&a};
@@ -638,6 +650,7 @@ extern "C" ptp_status ptp_last_stats(ptp_toplesets_t *t, void *stream, ptp_stats
     st->fp64_solves = (int64_t)h.fp64;
     st->rho = info[0];
     st->status = h.status;
+    st->checks = h.checks;
     return (ptp_status)h.status;
 }
 
@@ -704,6 +717,7 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
         a.perm = nullptr;
         a.lab0 = a.lab1 = nullptr;
         a.band_mode = params->band_mode;
+        a.sched = params->schedule;
         void *args[] = {(void *)&a};
         if (params->ev_begin) {
             ce = cudaEventRecord((cudaEvent_t)params->ev_begin, s);
@@ -855,6 +869,7 @@ extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params 
     a.perm = nullptr;
     a.lab0 = a.lab1 = nullptr;
     a.band_mode = params->band_mode;
+    a.sched = params->schedule;
     void *args[] = {(void *)&a};
     if (params->ev_begin) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_begin, s));
     PTP_TRY(cudaLaunchCooperativeKernel((const void *)ptp_window<false, false>, dim3(grid), dim3(DIST_THREADS), args, 0, s));
@@ -876,5 +891,6 @@ extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params 
     stats->fp64_solves = (int64_t)h.fp64;
     stats->rho = info[0];
     stats->status = h.status;
+    stats->checks = h.checks;
     return (ptp_status)h.status;
 }

@@ -50,6 +50,7 @@ struct ptp_ctrl {
     unsigned long long active;   // recomputed vertex updates
     unsigned long long changed;  // updates that lowered d
     unsigned long long fp64;     // triangle solves taken in FP64
+    long long checks;            // iterations that applied the test of Eq. lower_band
 };
 
 // One-ring slot layout of a renumbered vertex: its neighbours in cyclic

@@ -43,6 +43,7 @@ extern "C" ptp_status ptp_params_default(ptp_params *p) {
     p->trace_cap = 0;
     p->ev_begin = nullptr;
     p->ev_end = nullptr;
+    p->schedule = nullptr;
     return PTP_OK;
 }
 

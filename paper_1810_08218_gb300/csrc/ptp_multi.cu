@@ -165,6 +165,7 @@ void fill_stats(ptp_stats *st, const ptp_ctrl &h, int rho) {
     st->fp64_solves = (int64_t)h.fp64;
     st->rho = rho;
     st->status = h.status;
+    st->checks = h.checks;
 }
 
 }  // namespace
@@ -234,6 +235,7 @@ extern "C" ptp_status ptp_fps(ptp_mesh *mesh, int32_t first, int32_t n_samples, 
     ptp_params p = *params;
     p.trace = nullptr;  // one trace per map would overwrite itself
     p.trace_cap = 0;
+    p.schedule = nullptr;  // a schedule is per source set
     cudaStream_t us = (cudaStream_t)stream;
     const int n = (int)mesh->n;
     PTP_CHECK(ptp_internal_prepare());
@@ -307,5 +309,6 @@ extern "C" ptp_status ptp_fps(ptp_mesh *mesh, int32_t first, int32_t n_samples, 
     stats->fp64_solves = h.fp64;
     stats->rho = h.rho;
     stats->status = h.status;
+    stats->checks = 0;
     return (ptp_status)h.status;
 }
