@@ -40,7 +40,7 @@ WORKLOADS = {
     "sphere_l7": "unit icosphere level 7 (163,842 vertices, 327,680 triangles), one seeded source, eps=1e-3",
     "flat65": "65x65 jittered unit square (4,225 vertices, 8,192 triangles), centre source, eps=1e-3",
 }
-# Algorithmic bytes per band vertex-update (SURVEY 8(d) traffic model): its
+# Algorithmic bytes per band vertex-update (the per-update traffic model): its
 # float4 position 16 B + d_{k-1} 4 B + d_k 4 B + row offset 4 B + six incident
 # pairs 48 B.  Neighbour data is counted once, under the neighbour's own update.
 BYTES_PER_UPDATE = 76

@@ -57,6 +57,7 @@ enum { PTP_HOST = 0, PTP_DEVICE = 1 };
 
 typedef struct ptp_mesh ptp_mesh;
 typedef struct ptp_toplesets_s ptp_toplesets_t;
+typedef struct ptp_batch_s ptp_batch_t;
 
 /* Parameters of ptp_distance.  Fill with ptp_params_default first. */
 typedef struct ptp_params {
@@ -219,6 +220,43 @@ ptp_status ptp_distance(ptp_toplesets_t *tops, const ptp_params *params, float *
 #define PTP_NOALLOC_MAX_VERTS 1048576
 ptp_status ptp_distance_noalloc(ptp_toplesets_t *tops, const ptp_params *params, float *d_out, void *stream,
                                 ptp_stats *stats);
+
+/*
+ * Batched maps: up to PTP_BATCH_MAX independent single-source problems
+ * (different meshes, different sources, different sizes) solved by one
+ * persistent launch.  Each map follows the iteration of Sec. 3.2 with its
+ * own window (Eq. lower_band / upper_band) and its own iteration count, so
+ * every map's distances are bit for bit those ptp_distance returns for it
+ * alone; the maps share one grid barrier per iteration, which on meshes too
+ * small to fill the GPU turns many latency-bound launches into one.  (An
+ * addition of this library: the paper runs one map at a time.)
+ *
+ * ptp_batch_create copies the count toplesets handles' renumbered layouts
+ * into one concatenated device layout (208 bytes per vertex plus 8 per
+ * corner); the handles may be destroyed afterwards.  All handles must live on
+ * one device, with fewer than 2^26 vertices and 2^31 corners in total
+ * (PTP_ERR_TOO_LARGE otherwise); count in [1, PTP_BATCH_MAX] (PTP_ERR_ARG).
+ * The handle belongs to the caller: ptp_batch_destroy frees it, after its
+ * work on the creation stream has finished.
+ *
+ * ptp_distance_batch runs the maps with `params` shared by all of them
+ * (eps, eps_abs, max_iter, grid, band_mode and the events as in
+ * ptp_distance; trace and schedule must be NULL, else PTP_ERR_ARG).
+ *  d_out   host array of count DEVICE pointers; d_out[b] receives map b's
+ *          [n_verts_b] float32 distances in its mesh's vertex order.
+ *  stats   NULL or an array of count records: per map iterations,
+ *          band_updates, rho, status and checks; active_updates, changed and
+ *          fp64_solves hold the batch totals.
+ * Blocks until the launch has finished (it reads every map's status).
+ * Returns PTP_OK when every map converged, PTP_ERR_NOT_CONVERGED when some
+ * map reached max_iter (all distances written), PTP_ERR_TIMEOUT when a
+ * device-side wait hit its limit.
+ */
+#define PTP_BATCH_MAX 32
+ptp_status ptp_batch_create(ptp_toplesets_t *const *tops, int32_t count, void *stream, ptp_batch_t **out);
+ptp_status ptp_distance_batch(ptp_batch_t *batch, const ptp_params *params, float *const *d_out, void *stream,
+                              ptp_stats *stats);
+ptp_status ptp_batch_destroy(ptp_batch_t *batch);
 
 /*
  * Geodesic Voronoi regions (Sec. 4.3, Voronoi diagrams from farthest-point

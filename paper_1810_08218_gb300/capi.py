@@ -90,6 +90,9 @@ def load(path: str | None = None):
             "ptp_distance": (st, [P, P, P, P, P]),
             "ptp_last_stats": (st, [P, P, P]),
             "ptp_distance_noalloc": (st, [P, P, P, P, P]),
+            "ptp_batch_create": (st, [P, i32, P, P]),
+            "ptp_distance_batch": (st, [P, P, P, P, P]),
+            "ptp_batch_destroy": (st, [P]),
             "ptp_voronoi": (st, [P, P, i32, ctypes.c_int, P, P, P, P, P]),
             "ptp_window_features": (st, [P, P, P]),
             "ptp_mlp_infer": (st, [P, P, i32, P, ctypes.c_float, i32, P, P]),
@@ -186,6 +189,19 @@ class Toplesets:
         if getattr(self, "handle", None):
             try:
                 ptp_toplesets_destroy(self)
+            except Exception:
+                pass
+
+
+class Batch:
+    def __init__(self, handle: ctypes.c_void_p, sizes: list[int]):
+        self.handle = handle
+        self.sizes = sizes  # vertices per map
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                ptp_batch_destroy(self)
             except Exception:
                 pass
 
@@ -289,6 +305,38 @@ def ptp_distance_noalloc(tops: Toplesets, params: Params, d_out, stream=None, st
 
 
 PTP_NOALLOC_MAX_VERTS = 1048576
+
+
+PTP_BATCH_MAX = 32
+
+
+def ptp_batch_create(tops: list[Toplesets], stream=None) -> Batch:
+    """Concatenate up to PTP_BATCH_MAX toplesets handles into one batch."""
+    arr = (ctypes.c_void_p * len(tops))(*[t.handle.value if isinstance(t.handle, ctypes.c_void_p) else t.handle
+                                          for t in tops])
+    h = ctypes.c_void_p()
+    _check(load().ptp_batch_create(arr, len(tops), _stream_ptr(stream), ctypes.byref(h)), "ptp_batch_create")
+    return Batch(h, [t.mesh.n for t in tops])
+
+
+def ptp_batch_destroy(batch: Batch) -> None:
+    h, batch.handle = batch.handle, None
+    if h:
+        _check(load().ptp_batch_destroy(h), "ptp_batch_destroy")
+
+
+def ptp_distance_batch(batch: Batch, params: Params, d_outs, stream=None, stats: bool = True,
+                       ok=(PTP_OK,)) -> list[dict] | None:
+    """All maps of the batch in one launch; d_outs[b] is a float32 CUDA
+    tensor of map b's vertex count.  Returns per-map statistics."""
+    if len(d_outs) != len(batch.sizes):
+        raise ValueError("one output per map")
+    ptrs = (ctypes.c_void_p * len(d_outs))(*[d.data_ptr() for d in d_outs])
+    st = (Stats * len(d_outs))() if stats else None
+    code = load().ptp_distance_batch(batch.handle, ctypes.byref(params), ptrs, _stream_ptr(stream),
+                                     st if st is not None else None)
+    _check(code, "ptp_distance_batch", ok)
+    return [x.as_dict() for x in st] if st is not None else None
 
 
 def ptp_voronoi(mesh: Mesh, seeds, params: Params, d_out=None, label_out=None, stream=None, stats: bool = True,

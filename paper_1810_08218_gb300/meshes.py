@@ -265,3 +265,26 @@ def terrain_4096(seed: int = 0):
     amplitude 0.1, one seeded random source."""
     V, F = terrain(4096, 4096, octaves=8, amplitude=0.1, seed=seed)
     return V, F, np.array([random_source(V.shape[0], seed + 1)], dtype=np.int32)
+
+
+def uneven_batch(count: int = 32, n_min: int = 10_000, n_max: int = 2_000_000, seed: int = 0):
+    """A batch of independent single-source problems of uneven size: vertex
+    counts log-uniform in [n_min, n_max], even entries jittered unit-square
+    grids (jitter +-0.2 spacing, aspect ratio in [1, 2]), odd entries noisy
+    tori (R=1, r=0.4, radial noise +-0.01 r), each with one seeded random
+    source.  Returns a list of ``(V, F, S)``."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(count):
+        n = float(np.exp(rng.uniform(math.log(n_min), math.log(n_max))))
+        s = int(rng.integers(0, 2**31 - 1))
+        if b % 2 == 0:
+            aspect = float(rng.uniform(1.0, 2.0))
+            ny = max(3, int(round(math.sqrt(n / aspect))))
+            nx = max(3, int(round(n / ny)))
+            V, F = grid(nx, ny, jitter=0.2, seed=s)
+        else:
+            side = max(4, int(round(math.sqrt(n))))
+            V, F = torus(side, side, 1.0, 0.4, noise=0.01, seed=s)
+        out.append((V, F, np.array([random_source(V.shape[0], s + 1)], dtype=np.int32)))
+    return out

@@ -51,3 +51,21 @@ def test_host_only_entry_points(lib):
     out = ctypes.c_void_p()
     assert lib.ptp_mesh_create(None, 10, None, 1, 0, None, ctypes.byref(out)) == capi.PTP_ERR_ARG
     assert lib.ptp_params_default(None) == capi.PTP_ERR_ARG
+
+
+def test_batch_argument_errors_before_cuda(lib):
+    from paper_1810_08218_gb300 import capi
+
+    out = ctypes.c_void_p()
+    lib.ptp_batch_create.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.ptp_batch_create(None, 1, None, ctypes.byref(out)) == capi.PTP_ERR_ARG
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.ptp_batch_create(arr, 1, None, ctypes.byref(out)) == capi.PTP_ERR_ARG
+    assert lib.ptp_batch_create(arr, 0, None, ctypes.byref(out)) == capi.PTP_ERR_ARG
+    assert lib.ptp_batch_create(arr, 33, None, ctypes.byref(out)) == capi.PTP_ERR_ARG
+    assert lib.ptp_batch_create(arr, 1, None, None) == capi.PTP_ERR_ARG
+    lib.ptp_distance_batch.argtypes = [ctypes.c_void_p] * 5
+    p = capi.Params()
+    assert lib.ptp_distance_batch(None, ctypes.byref(p), None, None, None) == capi.PTP_ERR_ARG
+    lib.ptp_batch_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.ptp_batch_destroy(None) == capi.PTP_ERR_ARG
