@@ -67,7 +67,8 @@ typedef struct ptp_params {
                           |d_k - d_{k-1}| < eps * d_{k-1} + eps_abs or the change
                           is exactly 0 (paper: eps_abs = 0)                        */
     int64_t max_iter;  /* iteration cap; 0 = 8 * rho + 64                          */
-    int32_t block;     /* threads per CTA of the window kernel; 0 = auto           */
+    int32_t block;     /* threads per CTA of the window kernel: 0 = 512, else a
+                          multiple of 32 in [64, 512] (see ptp_autotune)        */
     int32_t grid;      /* CTAs of the window kernel; 0 = all co-resident CTAs      */
     int32_t band_mode; /* 0: the paper's dynamic band (Eq. lower_band); 1: the
                           fixed band of the complexity analysis (Sec. 5), lower
@@ -257,6 +258,32 @@ ptp_status ptp_batch_create(ptp_toplesets_t *const *tops, int32_t count, void *s
 ptp_status ptp_distance_batch(ptp_batch_t *batch, const ptp_params *params, float *const *d_out, void *stream,
                               ptp_stats *stats);
 ptp_status ptp_batch_destroy(ptp_batch_t *batch);
+
+/*
+ * Launch-shape autotuner for ptp_distance or ptp_distance_batch (an addition
+ * of this library; the paper has no counterpart).  The iteration of Sec. 3.2
+ * fixes what is computed; the threads per CTA and the number of CTAs of the
+ * window kernel only change how fast, and every shape gives bit-identical
+ * distances.  Exactly one of tops / batch is non-NULL.  Each candidate shape
+ * (CTAs of 512, 256, 128 threads; all co-resident CTAs, one per SM, 1/2, 1/4
+ * and 1/8 of the SMs, 8 CTAs) runs the caller's problem `reps` times (0 = 3,
+ * at most 100) with the other fields of *params, timed on `stream` by CUDA
+ * events around the window kernel; the median decides.  The fastest shape is
+ * written to params->block and params->grid and, if result is non-NULL, to
+ * *result.  Trial outputs go to a scratch allocation, so no output buffer
+ * of the caller is written; ptp_last_stats(tops) afterwards describes the
+ * last trial run.  Blocks.  Returns the first failing status of a trial run
+ * (PTP_ERR_NOT_CONVERGED counts as success).
+ */
+typedef struct ptp_tune_result {
+    int32_t block;     /* threads per CTA of the fastest shape              */
+    int32_t grid;      /* CTAs of the fastest shape                         */
+    float ms;          /* its median window-kernel time                     */
+    float ms_default;  /* median time of the default shape (512, all CTAs)  */
+    int32_t tried;     /* shapes timed                                      */
+} ptp_tune_result;
+ptp_status ptp_autotune(ptp_toplesets_t *tops, ptp_batch_t *batch, ptp_params *params, int32_t reps, void *stream,
+                        ptp_tune_result *result);
 
 /*
  * Geodesic Voronoi regions (Sec. 4.3, Voronoi diagrams from farthest-point

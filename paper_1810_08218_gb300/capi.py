@@ -55,6 +55,14 @@ class Stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("ms_default", ctypes.c_float), ("tried", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 TRACE_DTYPE = np.dtype([("i", np.int32), ("j", np.int32), ("active", np.int32), ("changed", np.int32),
                         ("maxrel", np.float32), ("advanced", np.int32), ("errsum", np.float64)])
 
@@ -93,6 +101,7 @@ def load(path: str | None = None):
             "ptp_batch_create": (st, [P, i32, P, P]),
             "ptp_distance_batch": (st, [P, P, P, P, P]),
             "ptp_batch_destroy": (st, [P]),
+            "ptp_autotune": (st, [P, P, P, i32, P, P]),
             "ptp_voronoi": (st, [P, P, i32, ctypes.c_int, P, P, P, P, P]),
             "ptp_window_features": (st, [P, P, P]),
             "ptp_mlp_infer": (st, [P, P, i32, P, ctypes.c_float, i32, P, P]),
@@ -337,6 +346,18 @@ def ptp_distance_batch(batch: Batch, params: Params, d_outs, stream=None, stats:
                                      st if st is not None else None)
     _check(code, "ptp_distance_batch", ok)
     return [x.as_dict() for x in st] if st is not None else None
+
+
+def ptp_autotune(target, params: Params, reps: int = 3, stream=None) -> dict:
+    """Time the window kernel's launch shapes on `target` (a Toplesets or a
+    Batch), write the fastest into params.block / params.grid and return
+    the timings."""
+    r = TuneResult()
+    tops = target.handle if isinstance(target, Toplesets) else None
+    batch = target.handle if isinstance(target, Batch) else None
+    _check(load().ptp_autotune(tops, batch, ctypes.byref(params), reps, _stream_ptr(stream), ctypes.byref(r)),
+           "ptp_autotune")
+    return r.as_dict()
 
 
 def ptp_voronoi(mesh: Mesh, seeds, params: Params, d_out=None, label_out=None, stream=None, stats: bool = True,

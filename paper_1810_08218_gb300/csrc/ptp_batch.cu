@@ -51,6 +51,7 @@ struct ptp_batch_s {
     int64_t N;  // total vertices
     int64_t C;  // total corners
     ptp_batch_layout L;
+    int64_t n[PTP_BATCH_MAX];  // vertices per map
 };
 
 namespace {
@@ -410,6 +411,21 @@ void free_layout(ptp_batch_layout &L, cudaStream_t s) {
 
 }  // namespace
 
+ptp_status ptp_internal_batch_shape(const ptp_batch_t *bt, int *device, int *count, int64_t *sizes) {
+    if (!bt) return PTP_ERR_ARG;
+    *device = bt->device;
+    *count = bt->count;
+    if (sizes)
+        for (int b = 0; b < bt->count; ++b) sizes[b] = bt->n[b];
+    return PTP_OK;
+}
+
+ptp_status ptp_internal_window_occupancy_batch(int block, int *per_sm) {
+    *per_sm = 0;
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ptp_window_batch, block, 0));
+    return PTP_OK;
+}
+
 extern "C" ptp_status ptp_batch_create(ptp_toplesets_t *const *tops, int32_t count, void *stream, ptp_batch_t **out) {
     if (!out) return PTP_ERR_ARG;
     *out = nullptr;
@@ -443,6 +459,7 @@ extern "C" ptp_status ptp_batch_create(ptp_toplesets_t *const *tops, int32_t cou
     int64_t base = 0, cbase = 0, ostart = 0;
     for (int b = 0; b < count && e == cudaSuccess; ++b) {
         const ptp_toplesets_t *t = tops[b];
+        bt->n[b] = t->n;
         const int64_t work = t->n > t->ncorner ? t->n : t->ncorner;
         batch_copy<<<blocks_for(work, 256, bt->device), 256, 0, s>>>(
             (int)N, (int)t->n, (int)base, (int)cbase, (int)t->ncorner, (int)ostart, b, t->pos, t->ring, t->meta,
@@ -478,7 +495,8 @@ extern "C" ptp_status ptp_distance_batch(ptp_batch_t *bt, const ptp_params *para
         if (!d_out[b]) return PTP_ERR_ARG;
     if (!(params->eps >= 0.0) || !(params->eps_abs >= 0.0) || params->max_iter < 0) return PTP_ERR_ARG;
     if (params->band_mode != 0 && params->band_mode != 1) return PTP_ERR_ARG;
-    if (params->block != 0 && params->block != DIST_THREADS) return PTP_ERR_ARG;
+    const int block = window_block(params->block);
+    if (block < 0) return PTP_ERR_ARG;
     if (params->trace || params->schedule) return PTP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t N = bt->N;
@@ -511,7 +529,7 @@ extern "C" ptp_status ptp_distance_batch(ptp_batch_t *bt, const ptp_params *para
         e = cudaGetLastError();
     }
     int per_sm = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window_batch, DIST_THREADS, 0);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window_batch, block, 0);
     if (e == cudaSuccess && per_sm < 1) st = PTP_ERR_CUDA;
     if (e == cudaSuccess && st == PTP_OK) {
         int grid = per_sm * ptp_num_sms(dev);
@@ -545,7 +563,7 @@ extern "C" ptp_status ptp_distance_batch(ptp_batch_t *bt, const ptp_params *para
         void *args[] = {(void *)&ba};
         if (params->ev_begin) e = cudaEventRecord((cudaEvent_t)params->ev_begin, s);
         if (e == cudaSuccess) {
-            e = cudaLaunchCooperativeKernel((const void *)ptp_window_batch, dim3(grid), dim3(DIST_THREADS), args, 0, s);
+            e = cudaLaunchCooperativeKernel((const void *)ptp_window_batch, dim3(grid), dim3(block), args, 0, s);
             ptp_count_launches(1);
         }
         if (e == cudaSuccess && params->ev_end) e = cudaEventRecord((cudaEvent_t)params->ev_end, s);

@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                 float bm = 0.0f;
                 double bs = 0.0;
                 int ba = 0, bc = 0;
-                for (int w = 0; w < DIST_THREADS / 32; ++w) {
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
                     bm = fmaxf(bm, s_max[w]);
                     bs += s_sum[w];
                     ba += s_cnt[0][w];
@@ -368,8 +368,10 @@ ptp_status ptp_internal_window_multi(const ptp_mesh *mesh, ptp_multi_bufs *b, co
     ptp_count_launches(2);
     PTP_TRY(cudaGetLastError());
     const void *fn = labels ? (const void *)ptp_window<true, true> : (const void *)ptp_window<true, false>;
+    const int block = window_block(params->block);
+    if (block < 0) return PTP_ERR_ARG;
     int per_sm = 0;
-    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, DIST_THREADS, 0));
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0));
     if (per_sm < 1) return PTP_ERR_CUDA;
     int grid = per_sm * ptp_num_sms(dev);
     if (params->grid > 0 && params->grid < grid) grid = params->grid;
@@ -402,8 +404,14 @@ ptp_status ptp_internal_window_multi(const ptp_mesh *mesh, ptp_multi_bufs *b, co
     if (params->trace && params->trace_cap > 0)
         PTP_TRY(cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s));
     void *args[] = {(void *)&a};
-    PTP_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(DIST_THREADS), args, 0, s));
+    PTP_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, s));
     ptp_count_launches(1);
+    return PTP_OK;
+}
+
+ptp_status ptp_internal_window_occupancy(int block, int *per_sm) {
+    *per_sm = 0;
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ptp_window<false, false>, block, 0));
     return PTP_OK;
 }
 
@@ -431,7 +439,8 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
     if (!t || !params || !d_out) return PTP_ERR_ARG;
     if (!(params->eps >= 0.0) || !(params->eps_abs >= 0.0) || params->max_iter < 0 || params->trace_cap < 0)
         return PTP_ERR_ARG;
-    if (params->block != 0 && params->block != DIST_THREADS) return PTP_ERR_ARG;
+    const int block = window_block(params->block);
+    if (block < 0) return PTP_ERR_ARG;
     if (params->band_mode != 0 && params->band_mode != 1) return PTP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = t->n;
@@ -459,7 +468,7 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
         if (ce != cudaSuccess) break;
 
         int per_sm = 0;
-        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false>, DIST_THREADS, 0);
+        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false>, block, 0);
         if (ce != cudaSuccess) break;
         if (per_sm < 1) { st = PTP_ERR_CUDA; break; }
         int grid = per_sm * ptp_num_sms(dev);
@@ -495,7 +504,7 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
             ce = cudaEventRecord((cudaEvent_t)params->ev_begin, s);
             if (ce != cudaSuccess) break;
         }
-        ce = cudaLaunchCooperativeKernel((const void *)ptp_window<false, false>, dim3(grid), dim3(DIST_THREADS), args, 0, s);
+        ce = cudaLaunchCooperativeKernel((const void *)ptp_window<false, false>, dim3(grid), dim3(block), args, 0, s);
         if (ce != cudaSuccess) break;
         ptp_count_launches(1);
         if (params->ev_end) {
@@ -589,7 +598,8 @@ extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params 
     if (!t || !params || !d_out) return PTP_ERR_ARG;
     if (!(params->eps >= 0.0) || !(params->eps_abs >= 0.0) || params->max_iter < 0 || params->trace_cap < 0)
         return PTP_ERR_ARG;
-    if (params->block != 0 && params->block != DIST_THREADS) return PTP_ERR_ARG;
+    const int block = window_block(params->block);
+    if (block < 0) return PTP_ERR_ARG;
     if (params->band_mode != 0 && params->band_mode != 1) return PTP_ERR_ARG;
     if (t->n > (int64_t)PTP_NOALLOC_MAX_VERTS) return PTP_ERR_TOO_LARGE;
     cudaStream_t s = (cudaStream_t)stream;
@@ -612,7 +622,7 @@ extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params 
     ptp_count_launches(1);
     PTP_TRY(cudaGetLastError());
     int per_sm = 0;
-    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false>, DIST_THREADS, 0));
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false>, block, 0));
     if (per_sm < 1) return PTP_ERR_CUDA;
     int grid = per_sm * ptp_num_sms(dev);
     if (params->grid > 0 && params->grid < grid) grid = params->grid;
@@ -644,7 +654,7 @@ extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params 
     a.sched = params->schedule;
     void *args[] = {(void *)&a};
     if (params->ev_begin) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_begin, s));
-    PTP_TRY(cudaLaunchCooperativeKernel((const void *)ptp_window<false, false>, dim3(grid), dim3(DIST_THREADS), args, 0, s));
+    PTP_TRY(cudaLaunchCooperativeKernel((const void *)ptp_window<false, false>, dim3(grid), dim3(block), args, 0, s));
     ptp_count_launches(1);
     if (params->ev_end) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_end, s));
     scatter_out<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, dbuf, dbuf + n, ctrl, d_out);

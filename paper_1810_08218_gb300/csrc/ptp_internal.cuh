@@ -134,6 +134,14 @@ __host__ __device__ inline int ptp_final_buffer(long long iterations) { return (
 
 int ptp_num_sms(int device);
 
+// Co-resident CTAs per SM of the single-map / batched window kernel
+// launched with `block` threads; 0 when it cannot launch.
+ptp_status ptp_internal_window_occupancy(int block, int *per_sm);
+ptp_status ptp_internal_window_occupancy_batch(int block, int *per_sm);
+
+// Device of a batch handle and its maps' vertex counts (sizes may be NULL).
+ptp_status ptp_internal_batch_shape(const ptp_batch_t *batch, int *device, int *count, int64_t *sizes);
+
 // Counts kernel launches issued by the library (ptp_kernel_launches).
 void ptp_count_launches(int n);
 

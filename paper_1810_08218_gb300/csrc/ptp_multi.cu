@@ -153,7 +153,7 @@ ptp_status check_params(const ptp_params *p) {
     if (!p) return PTP_ERR_ARG;
     if (!(p->eps >= 0.0) || !(p->eps_abs >= 0.0) || p->max_iter < 0 || p->trace_cap < 0) return PTP_ERR_ARG;
     if (p->band_mode != 0 && p->band_mode != 1) return PTP_ERR_ARG;
-    if (p->block != 0 && p->block != 512) return PTP_ERR_ARG;
+    if (p->block != 0 && (p->block < 64 || p->block > 512 || p->block % 32 != 0)) return PTP_ERR_ARG;
     return PTP_OK;
 }
 

@@ -232,6 +232,15 @@ __device__ __forceinline__ int warp_sum_i(int v) {
 #define PTP_DIST_MIN_BLOCKS 1
 #endif
 
+// Threads per CTA of a window launch: 0 selects DIST_THREADS; otherwise a
+// multiple of 32 in [64, DIST_THREADS] (the kernels index by blockDim and
+// size their shared arrays for DIST_THREADS); -1 if invalid.
+inline int window_block(int32_t requested) {
+    if (requested == 0) return DIST_THREADS;
+    if (requested < 64 || requested > DIST_THREADS || requested % 32 != 0) return -1;
+    return requested;
+}
+
 // Band bounds of one iteration.
 struct Band {
     int copy_lo;  // start of the topleset retired after the previous iteration

@@ -69,3 +69,13 @@ def test_batch_argument_errors_before_cuda(lib):
     assert lib.ptp_distance_batch(None, ctypes.byref(p), None, None, None) == capi.PTP_ERR_ARG
     lib.ptp_batch_destroy.argtypes = [ctypes.c_void_p]
     assert lib.ptp_batch_destroy(None) == capi.PTP_ERR_ARG
+
+
+def test_autotune_argument_errors_before_cuda(lib):
+    from paper_1810_08218_gb300 import capi
+
+    lib.ptp_autotune.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    p = capi.Params()
+    assert lib.ptp_autotune(None, None, ctypes.byref(p), 3, None, None) == capi.PTP_ERR_ARG  # neither target
+    assert lib.ptp_autotune(ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.byref(p), 3, None, None) == capi.PTP_ERR_ARG
+    assert lib.ptp_autotune(ctypes.c_void_p(8), None, None, 3, None, None) == capi.PTP_ERR_ARG
