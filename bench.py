@@ -78,7 +78,7 @@ def _peaks():
 
 def _kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("ptp_distance.cu", "ptp_internal.cuh"):
+    for f in ("ptp_distance.cu", "ptp_update.cuh", "ptp_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1810_08218_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()

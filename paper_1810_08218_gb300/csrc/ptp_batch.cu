@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(DIST_THREADS, 1) ptp_window_batch(BatchArgs ba
                 float4 g[PTP_TRI];
 #pragma unroll
                 for (int t = 0; t < PTP_TRI; ++t)
-                    g[t] = t < mm - 1 ? __ldg(a.tgeom + (size_t)t * a.n + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    g[t] = __ldg(a.tgeom + (size_t)t * a.n + u);  // every slot is written: no wait on meta
                 const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
                 const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
                 int label = 0;

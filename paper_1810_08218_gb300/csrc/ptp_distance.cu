@@ -96,106 +96,154 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         float maxrel = 0.0f;
         double errsum = 0.0;
         const int base = start & ~31;
-        // chunks of this CTA's warps: c = gwarp + m * nwarps, m = 0, 1, ...
         const int nchunks = bd.hi > base ? (bd.hi - base + 31) >> 5 : 0;
-        const int rounds_m = nchunks > gwarp ? (nchunks - gwarp + nwarps - 1) / nwarps : 0;
-        // every warp of the CTA must run the same number of rounds
-        const int cta_m = (nchunks > (int)blockIdx.x) ? (nchunks - (int)blockIdx.x + nwarps - 1) / nwarps : 0;
-        for (int m0 = 0; m0 < cta_m; m0 += ROUND_CHUNKS) {
-            if (threadIdx.x == 0) s_nq = 0;
-            __syncthreads();
-            // pass 1: state of each band vertex; queue the ones to recompute.
-            // The state of P1_BATCH chunks is loaded before any is used.
-            for (int m = m0; m < m0 + ROUND_CHUNKS && m < rounds_m; m += P1_BATCH) {
-                int pp[P1_BATCH], uu[P1_BATCH], ns[P1_BATCH], cg[P1_BATCH];
-                float dold[P1_BATCH];
-                bool live[P1_BATCH];
+
+        // Recompute band vertex u from d_{k-1}, given its one-ring slots and
+        // geometry: write d_k (and its label), stamp the neighbours if it
+        // changed, and apply the relative-change test to V_{i_{k-1}}.
+        auto recompute = [&](int u, bool in_vi, float dold, int meta, int4 r0, int4 r1, float4 l0, float4 l1,
+                             const float4 *g) {
+            const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+            const int m = meta & PTP_META_CNT;
+            int label = LABELS ? __ldcg(lp + u) : 0;
+            float dnew;
+            if (meta & PTP_META_GENERAL) dnew = update_general(a, u, dold, dp, lp, LABELS ? &label : nullptr, nfp64);
+            else dnew = update_ring<LABELS>(a, u, ids, el, g, m, dold, dp, lp, label, nfp64);
+            ++n_active;
+            dnx[u] = dnew;
+            if (LABELS) lnx[u] = label;
+            if (dnew != dold) {
+                ++n_changed;
+                a.chg[u] = (int)k;
+                if (meta & PTP_META_GENERAL) {
+                    stamp_general(a, u, (int)k);
+                } else {
 #pragma unroll
-                for (int q = 0; q < P1_BATCH; ++q) {
-                    pp[q] = base + (gwarp + (m + q) * nwarps) * 32 + lane;
-                    const bool ok = m + q < rounds_m && pp[q] >= start && pp[q] < bd.hi && pp[q] >= nsrc;
-                    live[q] = ok && pp[q] >= bd.lo;
-                    uu[q] = ok ? vertex_at(pp[q]) : 0;
+                    for (int t = 0; t < PTP_RING; ++t)
+                        if (t < m) a.nstamp[ids[t]] = (int)k;
                 }
-#pragma unroll
-                for (int q = 0; q < P1_BATCH; ++q) {
-                    const bool ok = m + q < rounds_m && pp[q] >= start && pp[q] < bd.hi && pp[q] >= nsrc;
-                    dold[q] = ok ? __ldcg(dp + uu[q]) : 0.0f;
-                    ns[q] = live[q] ? __ldcg(a.nstamp + uu[q]) : -2;
-                    cg[q] = live[q] ? __ldcg(a.chg + uu[q]) : -2;
-                    if (ok && !live[q]) {  // retired after the previous iteration
-                        dnx[uu[q]] = dold[q];
-                        if (LABELS) lnx[uu[q]] = __ldcg(lp + uu[q]);
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < P1_BATCH; ++q) {
-                    const bool need = live[q] && ((entering && pp[q] >= bd.vj_beg) || ns[q] >= k - 1);
-                    if (live[q] && !need && cg[q] == k - 1) {
-                        dnx[uu[q]] = dold[q];
-                        if (LABELS) lnx[uu[q]] = __ldcg(lp + uu[q]);
-                    }
-                    const unsigned bal = __ballot_sync(0xffffffffu, need);
-                    if (bal) {
-                        int at = 0;
-                        if (lane == 0) at = atomicAdd(&s_nq, __popc(bal));
-                        at = __shfl_sync(0xffffffffu, at, 0);
-                        if (need)
-                            s_queue[at + __popc(bal & ((1u << lane) - 1u))] =
-                                make_int2(uu[q] | (pp[q] < bd.vi_end ? (int)0x80000000 : 0), __float_as_int(dold[q]));
+                if (in_vi && testing) {
+                    // relative-change test of Eq. lower_band, in FP64 (the
+                    // difference of two floats is exact in double)
+                    const double o = dold, delta = o - (double)dnew;
+                    if (!(isfinite(o) && delta < __dadd_rn(__dmul_rn(a.eps, o), a.eps_abs))) notconv = 1;
+                    if (a.trace) {
+                        const double rel = isfinite(o) ? (o > 0.0 ? delta / o : 0.0) : (double)INF;
+                        maxrel = fmaxf(maxrel, (float)rel);
+                        errsum += rel;
                     }
                 }
             }
-            __syncthreads();
-            // pass 2: recompute the queued vertices
-            const int nq = s_nq;
-            for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-                const int2 ent = s_queue[q];
-                const int u = ent.x & 0x7fffffff;
-                const bool in_vi = ent.x < 0;
-                const float dold = __int_as_float(ent.y);
-                const int meta = __ldg(a.meta + u);
-                const int4 r0 = __ldg(a.ring + u), r1 = __ldg(a.ring + a.n + u);
-                const float4 l0 = __ldg(a.elen + u), l1 = __ldg(a.elen + a.n + u);
-                const int m = meta & PTP_META_CNT;
+        };
+        // The geometry of every slot is loaded whatever the vertex's count:
+        // every slot is written, and the loads need not wait for meta.
+        auto load_slots = [&](int u, int &meta, int4 &r0, int4 &r1, float4 &l0, float4 &l1, float4 *g) {
+            meta = __ldg(a.meta + u);
+            r0 = __ldg(a.ring + u);
+            r1 = __ldg(a.ring + a.n + u);
+            l0 = __ldg(a.elen + u);
+            l1 = __ldg(a.elen + a.n + u);
+#pragma unroll
+            for (int t = 0; t < PTP_TRI; ++t) g[t] = __ldg(a.tgeom + (size_t)t * a.n + u);
+        };
+
+        if (nchunks <= nwarps) {
+            // Narrow band: at most one chunk per warp (c = gwarp).  The warp
+            // loads its chunk's state, one-ring slots and geometry in one round
+            // trip and recomputes in place, with no queue and no CTA barrier
+            // between the passes; the extra geometry read for vertices that
+            // turn out not to need an update is small at this band width.
+            if (gwarp < nchunks) {
+                const int p = base + gwarp * 32 + lane;
+                const bool ok = p >= start && p < bd.hi && p >= nsrc;
+                const bool live = ok && p >= bd.lo;
+                const int u = ok ? vertex_at(p) : 0;
+                const float dold = ok ? __ldcg(dp + u) : 0.0f;
+                const int ns = live ? __ldcg(a.nstamp + u) : -2;
+                const int cg = live ? __ldcg(a.chg + u) : -2;
+                int meta = 0;
+                int4 r0 = make_int4(-1, -1, -1, -1), r1 = r0;
+                float4 l0 = make_float4(0.f, 0.f, 0.f, 0.f), l1 = l0;
                 float4 g[PTP_TRI];
 #pragma unroll
-                for (int t = 0; t < PTP_TRI; ++t)
-                    g[t] = t < m - 1 ? __ldg(a.tgeom + (size_t)t * a.n + u) : make_float4(0.f, 0.f, 0.f, 0.f);
-                const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-                const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
-                int label = LABELS ? __ldcg(lp + u) : 0;
-                float dnew;
-                if (meta & PTP_META_GENERAL) dnew = update_general(a, u, dold, dp, lp, LABELS ? &label : nullptr, nfp64);
-                else dnew = update_ring<LABELS>(a, u, ids, el, g, m, dold, dp, lp, label, nfp64);
-                ++n_active;
-                dnx[u] = dnew;
-                if (LABELS) lnx[u] = label;
-                if (dnew != dold) {
-                    ++n_changed;
-                    a.chg[u] = (int)k;
-                    if (meta & PTP_META_GENERAL) {
-                        stamp_general(a, u, (int)k);
-                    } else {
-                        const int cnt = meta & PTP_META_CNT;
+                for (int t = 0; t < PTP_TRI; ++t) g[t] = l0;
+                if (live) load_slots(u, meta, r0, r1, l0, l1, g);
+                if (ok && !live) {  // retired after the previous iteration
+                    dnx[u] = dold;
+                    if (LABELS) lnx[u] = __ldcg(lp + u);
+                }
+                const bool need = live && ((entering && p >= bd.vj_beg) || ns >= k - 1);
+                if (live && !need && cg == k - 1) {
+                    dnx[u] = dold;
+                    if (LABELS) lnx[u] = __ldcg(lp + u);
+                }
+                if (need) recompute(u, p < bd.vi_end, dold, meta, r0, r1, l0, l1, g);
+            }
+        } else {
+            // chunks of this CTA's warps: c = gwarp + m * nwarps, m = 0, 1, ...
+            const int rounds_m = nchunks > gwarp ? (nchunks - gwarp + nwarps - 1) / nwarps : 0;
+            // every warp of the CTA must run the same number of rounds
+            const int cta_m = (nchunks > (int)blockIdx.x) ? (nchunks - (int)blockIdx.x + nwarps - 1) / nwarps : 0;
+            for (int m0 = 0; m0 < cta_m; m0 += ROUND_CHUNKS) {
+                if (threadIdx.x == 0) s_nq = 0;
+                __syncthreads();
+                // pass 1: state of each band vertex; queue the ones to recompute.
+                // The state of P1_BATCH chunks is loaded before any is used.
+                for (int m = m0; m < m0 + ROUND_CHUNKS && m < rounds_m; m += P1_BATCH) {
+                    int pp[P1_BATCH], uu[P1_BATCH], ns[P1_BATCH], cg[P1_BATCH];
+                    float dold[P1_BATCH];
+                    bool live[P1_BATCH];
 #pragma unroll
-                        for (int t = 0; t < PTP_RING; ++t)
-                            if (t < cnt) a.nstamp[ids[t]] = (int)k;
+                    for (int q = 0; q < P1_BATCH; ++q) {
+                        pp[q] = base + (gwarp + (m + q) * nwarps) * 32 + lane;
+                        const bool ok = m + q < rounds_m && pp[q] >= start && pp[q] < bd.hi && pp[q] >= nsrc;
+                        live[q] = ok && pp[q] >= bd.lo;
+                        uu[q] = ok ? vertex_at(pp[q]) : 0;
                     }
-                    if (in_vi && testing) {
-                        // relative-change test of Eq. lower_band, in FP64 (the
-                        // difference of two floats is exact in double)
-                        const double o = dold, delta = o - (double)dnew;
-                        if (!(isfinite(o) && delta < __dadd_rn(__dmul_rn(a.eps, o), a.eps_abs))) notconv = 1;
-                        if (a.trace) {
-                            const double rel = isfinite(o) ? (o > 0.0 ? delta / o : 0.0) : (double)INF;
-                            maxrel = fmaxf(maxrel, (float)rel);
-                            errsum += rel;
+#pragma unroll
+                    for (int q = 0; q < P1_BATCH; ++q) {
+                        const bool ok = m + q < rounds_m && pp[q] >= start && pp[q] < bd.hi && pp[q] >= nsrc;
+                        dold[q] = ok ? __ldcg(dp + uu[q]) : 0.0f;
+                        ns[q] = live[q] ? __ldcg(a.nstamp + uu[q]) : -2;
+                        cg[q] = live[q] ? __ldcg(a.chg + uu[q]) : -2;
+                        if (ok && !live[q]) {  // retired after the previous iteration
+                            dnx[uu[q]] = dold[q];
+                            if (LABELS) lnx[uu[q]] = __ldcg(lp + uu[q]);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < P1_BATCH; ++q) {
+                        const bool need = live[q] && ((entering && pp[q] >= bd.vj_beg) || ns[q] >= k - 1);
+                        if (live[q] && !need && cg[q] == k - 1) {
+                            dnx[uu[q]] = dold[q];
+                            if (LABELS) lnx[uu[q]] = __ldcg(lp + uu[q]);
+                        }
+                        const unsigned bal = __ballot_sync(0xffffffffu, need);
+                        if (bal) {
+                            int at = 0;
+                            if (lane == 0) at = atomicAdd(&s_nq, __popc(bal));
+                            at = __shfl_sync(0xffffffffu, at, 0);
+                            if (need)
+                                s_queue[at + __popc(bal & ((1u << lane) - 1u))] =
+                                    make_int2(uu[q] | (pp[q] < bd.vi_end ? (int)0x80000000 : 0), __float_as_int(dold[q]));
                         }
                     }
                 }
+                __syncthreads();
+                // pass 2: recompute the queued vertices
+                const int nq = s_nq;
+                for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+                    const int2 ent = s_queue[q];
+                    const int u = ent.x & 0x7fffffff;
+                    int meta;
+                    int4 r0, r1;
+                    float4 l0, l1, g[PTP_TRI];
+                    load_slots(u, meta, r0, r1, l0, l1, g);
+                    recompute(u, ent.x < 0, __int_as_float(ent.y), meta, r0, r1, l0, l1, g);
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
         tot_active += n_active;
         tot_changed += n_changed;
