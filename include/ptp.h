@@ -12,10 +12,10 @@
  *   ptp_mesh_create   vertices + faces -> device mesh with the
  *                     vertex -> incident-triangle lists;
  *   ptp_toplesets     sources -> toplesets V_r (breadth-first levels,
- *                     Sec. 3.1 Definition) and the mesh renumbered in
- *                     topleset order (Sec. 3.3);
+ *                     Sec. 4.1 Definition) and the mesh renumbered in
+ *                     topleset order (Sec. 4.3);
  *   ptp_distance      the PTP iteration over the sliding update band
- *                     (Sec. 3.2, Eq. lower_band / upper_band) into a
+ *                     (Sec. 4.2, Eq. lower_band / upper_band) into a
  *                     caller-owned device buffer in the ORIGINAL vertex order.
  *   ptp_geodesic      all three stages in one call (host or device buffers).
  *
@@ -61,7 +61,7 @@ typedef struct ptp_batch_s ptp_batch_t;
 
 /* Parameters of ptp_distance.  Fill with ptp_params_default first. */
 typedef struct ptp_params {
-    double eps;        /* relative-change threshold of Eq. lower_band (Sec. 3.2);
+    double eps;        /* relative-change threshold of Eq. lower_band (Sec. 4.2);
                           the paper uses 1e-3 in all experiments                   */
     double eps_abs;    /* absolute slack: a vertex of V_{i_{k-1}} passes when
                           |d_k - d_{k-1}| < eps * d_{k-1} + eps_abs or the change
@@ -71,7 +71,7 @@ typedef struct ptp_params {
                           multiple of 32 in [64, 512] (see ptp_autotune)        */
     int32_t grid;      /* CTAs of the window kernel; 0 = all co-resident CTAs      */
     int32_t band_mode; /* 0: the paper's dynamic band (Eq. lower_band); 1: the
-                          fixed band of the complexity analysis (Sec. 5), lower
+                          fixed band of the complexity analysis (Sec. 6.1), lower
                           bound ceil(k / 2), no convergence test                   */
     int32_t reserved;  /* must be 0                                                */
     void *trace;       /* optional DEVICE buffer of trace_cap ptp_trace_rec, one per
@@ -113,7 +113,7 @@ typedef struct ptp_stats {
 /* Human-readable name of a status code (static storage). */
 const char *ptp_status_str(ptp_status s);
 
-/* Defaults: eps = 1e-3 and eps_abs = 0 (Sec. 3.2, the paper's setting),
+/* Defaults: eps = 1e-3 and eps_abs = 0 (Sec. 4.2, the paper's setting),
  * max_iter = 0 (auto), block = grid = 0 (auto), band_mode = 0, no trace, no
  * events. */
 ptp_status ptp_params_default(ptp_params *p);
@@ -123,7 +123,7 @@ ptp_status ptp_params_default(ptp_params *p);
 int64_t ptp_kernel_launches(void);
 
 /*
- * Build the device mesh (Sec. 3.1, T = (V, E, F); Sec. 3.3 stores it as a
+ * Build the device mesh (Sec. 3.1, T = (V, E, F); Sec. 4.3 stores it as a
  * compact half-edge structure, here as vertex -> incident-triangle lists).
  *  xyz    [n_verts * 3] float32, row-major vertex positions.
  *  faces  [n_faces * 3] int32, 0-based, either orientation.
@@ -143,10 +143,10 @@ ptp_status ptp_mesh_info(const ptp_mesh *mesh, int64_t *n_verts, int64_t *n_face
 ptp_status ptp_mesh_destroy(ptp_mesh *mesh);
 
 /*
- * Toplesets from the source set S (Sec. 3.1, Definition: V_0 = S and V_r the
+ * Toplesets from the source set S (Sec. 4.1, Definition: V_0 = S and V_r the
  * not yet visited neighbours of V_{r-1}), computed by a breadth-first search
  * on the device, and the mesh renumbered so that V_0, V_1, ... occupy
- * consecutive index ranges (Sec. 3.3, reordering for coalesced access).
+ * consecutive index ranges (Sec. 4.3, reordering for coalesced access).
  *  sources  [m] int32 vertex indices, m >= 1; duplicates are allowed.
  *  PTP_ERR_INDEX if a source is outside [0, n_verts); PTP_ERR_ARG if m < 1.
  *  Vertices not reachable from S are placed after the last topleset and get
@@ -171,10 +171,10 @@ ptp_status ptp_toplesets_info(ptp_toplesets_t *tops, void *stream, int32_t *rho,
 ptp_status ptp_toplesets_destroy(ptp_toplesets_t *tops);
 
 /*
- * PTP (Sec. 3.2): d_0 = +inf except d_0(S) = 0; iteration k recomputes, from
+ * PTP (Sec. 4.2): d_0 = +inf except d_0(S) = 0; iteration k recomputes, from
  * d_{k-1} only, every non-source vertex of the band
  * B = V_{i_{k-1}} u ... u V_{j_k} as the minimum of its old value and the
- * update step (Sec. 2.2, planar Eikonal solve under the monotonicity
+ * update step (Sec. 3.2, planar Eikonal solve under the monotonicity
  * condition Q X^T n < 0, else the edge fallback) over its incident
  * triangles; j_k = min(k, rho - 1) (Eq. upper_band) and i_k = i_{k-1} + 1
  * when every vertex of V_{i_{k-1}} passed the relative-change test
@@ -225,7 +225,7 @@ ptp_status ptp_distance_noalloc(ptp_toplesets_t *tops, const ptp_params *params,
 /*
  * Batched maps: up to PTP_BATCH_MAX independent single-source problems
  * (different meshes, different sources, different sizes) solved by one
- * persistent launch.  Each map follows the iteration of Sec. 3.2 with its
+ * persistent launch.  Each map follows the iteration of Sec. 4.2 with its
  * own window (Eq. lower_band / upper_band) and its own iteration count, so
  * every map's distances are bit for bit those ptp_distance returns for it
  * alone; the maps share one grid barrier per iteration, which on meshes too
@@ -261,7 +261,7 @@ ptp_status ptp_batch_destroy(ptp_batch_t *batch);
 
 /*
  * Launch-shape autotuner for ptp_distance or ptp_distance_batch (an addition
- * of this library; the paper has no counterpart).  The iteration of Sec. 3.2
+ * of this library; the paper has no counterpart).  The iteration of Sec. 4.2
  * fixes what is computed; the threads per CTA and the number of CTAs of the
  * window kernel only change how fast, and every shape gives bit-identical
  * distances.  Exactly one of tops / batch is non-NULL.  Each candidate shape
@@ -286,8 +286,8 @@ ptp_status ptp_autotune(ptp_toplesets_t *tops, ptp_batch_t *batch, ptp_params *p
                         ptp_tune_result *result);
 
 /*
- * Geodesic Voronoi regions (Sec. 4.3, Voronoi diagrams from farthest-point
- * samples): one multi-source PTP map from the m seeds (Sec. 3.4, multi-source
+ * Geodesic Voronoi regions (Sec. 5.3, Voronoi diagrams from farthest-point
+ * samples): one multi-source PTP map from the m seeds (Sec. 6.1.5, multi-source
  * problem; as in the paper's multi-source runs the vertices are not
  * rearranged), where every vertex also carries the index (0..m-1) of the seed
  * its distance came from: the label of the closer neighbour of the triangle
@@ -302,7 +302,7 @@ ptp_status ptp_voronoi(ptp_mesh *mesh, const int32_t *seeds, int32_t m, int ptr_
                        float *d_out, int32_t *label_out, void *stream, ptp_stats *stats);
 
 /*
- * Farthest-point sampling (Sec. 4.3 and App. A): S_1 = {first};
+ * Farthest-point sampling (Sec. 5.3 and App. A): S_1 = {first};
  * S_{i+1} = S_i + argmax_v d_{S_i}(v), each d_{S_i} a full multi-source PTP
  * map from all samples so far (ties: the smallest vertex index; an
  * unreachable vertex counts as infinitely far).  Everything stays on the
@@ -335,7 +335,7 @@ ptp_status ptp_fps(ptp_mesh *mesh, int32_t first, int32_t n_samples, const ptp_p
  * smallest triangle angle at V_r's vertices, std/mean of the Euclidean
  * distance from the first source over V_r (how far the topleset is from a
  * sphere around the source, i.e. from the distance isocurves, which the paper
- * ties to the iteration count, Sec. 4.2), and r / rho.  feat_out must hold
+ * ties to the iteration count, Sec. 5.2), and r / rho.  feat_out must hold
  * 6 * n_verts floats.  Asynchronous. */
 ptp_status ptp_window_features(ptp_toplesets_t *tops, float *feat_out, void *stream);
 

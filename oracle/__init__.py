@@ -71,7 +71,7 @@ def _ptr(a: np.ndarray):
 
 
 def update(x0, x1, x2, d1: float, d2: float) -> float:
-    """The per-triangle update step (Sec. 2.2) for vertex x0."""
+    """The per-triangle update step (Sec. 3.2) for vertex x0."""
     lib = _load()
     a0 = np.ascontiguousarray(x0, dtype=np.float64)
     a1 = np.ascontiguousarray(x1, dtype=np.float64)
@@ -121,9 +121,9 @@ class PTPResult:
 
 def ptp(V: np.ndarray, F: np.ndarray, sources, eps: float = 1e-3, eps_abs: float = 0.0,
         max_iter: int = 0, trace: bool = False, history: int = 0, band_mode: int = 0) -> PTPResult:
-    """Run the oracle PTP (Sec. 3.2) in FP64.  `history` > 0 keeps d_k for
+    """Run the oracle PTP (Sec. 4.2) in FP64.  `history` > 0 keeps d_k for
     k = 0 .. history-1 (tiny meshes only).  band_mode 1: the fixed band of
-    the complexity analysis (Sec. 5) instead of Eq. lower_band."""
+    the complexity analysis (Sec. 6.1) instead of Eq. lower_band."""
     lib = _load()
     V = np.ascontiguousarray(V, dtype=np.float64)
     F = np.ascontiguousarray(F, dtype=np.int32)

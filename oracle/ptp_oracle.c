@@ -10,20 +10,20 @@
  * from the library's product path.
  *
  * What it computes, step by step, in the paper's order:
- *   1. vertex -> incident-triangle lists (the mesh adjacency, Sec. 3.3 uses a
+ *   1. vertex -> incident-triangle lists (the mesh adjacency, Sec. 4.3 uses a
  *      compact half-edge structure; any incidence structure gives the same
  *      triangles);
- *   2. toplesets V_r by breadth-first search from the sources (Sec. 3.1,
+ *   2. toplesets V_r by breadth-first search from the sources (Sec. 4.1,
  *      Definition of the topleset: V_0 = S, V_r = unvisited neighbours of
  *      V_{r-1});
  *   3. the Jacobi iteration d_k = F(d_{k-1}) over the update band
- *      B = V_{i_{k-1}} u ... u V_{j_k} (Sec. 3.2), with the band bounds of
+ *      B = V_{i_{k-1}} u ... u V_{j_k} (Sec. 4.2), with the band bounds of
  *      Eq. (upper_band) and Eq. (lower_band);
  *   4. the per-triangle update step: the planar (linear) local solve of the
  *      Eikonal equation |grad d| = 1 (Sec. 2, Eq. 1) inside one triangle,
- *      kept only when the monotonicity condition Q X^T n < 0 of Sec. 2.2
+ *      kept only when the monotonicity condition Q X^T n < 0 of Sec. 3.2
  *      holds, else the edge (Dijkstra-like) fallback.  No unfolding or
- *      subdivision of obtuse triangles is done (Sec. 2.2, Sec. 4).
+ *      subdivision of obtuse triangles is done (Sec. 3.2, Sec. 5).
  *
  * Readings of points the paper leaves open are listed where they are used.
  */
@@ -50,7 +50,7 @@ static double dot3(const double *u, const double *v) {
 
 /*
  * Update step for vertex x0 of triangle (x0, x1, x2) with known distances
- * d1 at x1 and d2 at x2 (Sec. 2.2, the Kimmel-Sethian planar update).
+ * d1 at x1 and d2 at x2 (Sec. 3.2, the Kimmel-Sethian planar update).
  *
  * Model: d is linear on the triangle, d(x) = p + g.(x - x0), so with
  * X = [e1 e2], e_i = x_i - x0, t = (d1, d2)^T:  X^T g = t - p 1.  Restricted
@@ -133,7 +133,7 @@ int or_incident(int64_t n, int64_t nf, const int32_t *faces, int64_t *row, int32
 }
 
 /*
- * Toplesets (Sec. 3.1, Definition): level[v] = length of the shortest
+ * Toplesets (Sec. 4.1, Definition): level[v] = length of the shortest
  * edge path from v to the source set S in the mesh graph, by a FIFO
  * breadth-first search; V_0 = S.  Vertices not reachable from S get -1.
  * Returns rho, the number of toplesets (1 + the largest level), or a
@@ -197,7 +197,7 @@ static void update_vertex_all(int64_t v, const double *xyz, const int64_t *row, 
 }
 
 /*
- * PTP (Sec. 3.2).  Iteration k (k = 1, 2, ...) recomputes every non-source
+ * PTP (Sec. 4.2).  Iteration k (k = 1, 2, ...) recomputes every non-source
  * vertex of the band B = V_{i_{k-1}} u ... u V_{j_k} from d_{k-1} only
  * (Jacobi: each vertex's new value depends on the previous map alone),
  * then sets the band bounds:
@@ -216,7 +216,7 @@ static void update_vertex_all(int64_t v, const double *xyz, const int64_t *row, 
  * Optional history: d_hist[k*n + v] = d_k(v) for k = 0 .. hist_cap-1.
  * max_iter <= 0 means 8*rho + 64.
  * band_mode 1 replaces Eq. lower_band by the fixed band of the complexity
- * analysis (Sec. 5: the band holds the last k/2 toplesets), i.e. the lower
+ * analysis (Sec. 6.1: the band holds the last k/2 toplesets), i.e. the lower
  * bound after iteration k is ceil(k/2), with no convergence test.
  * Returns OR_OK, OR_NOT_CONVERGED (max_iter reached, d_out still written)
  * or a negative error.

@@ -1,6 +1,6 @@
 // Batched PTP: up to 32 independent maps (different meshes and sources) in
 // one persistent cooperative launch.  Every map keeps its own window
-// (i_k, j_k of Eq. lower_band / upper_band, Sec. 3.2) and its own iteration
+// (i_k, j_k of Eq. lower_band / upper_band, Sec. 4.2) and its own iteration
 // count K_b; the maps advance in lockstep under one grid barrier per
 // iteration, so the barrier and the dependent-load latency of an iteration
 // are paid once for the whole batch, while each map's iterates are exactly

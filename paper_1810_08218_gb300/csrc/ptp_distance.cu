@@ -1,4 +1,4 @@
-// The PTP iteration (Sec. 3.2) over the sliding update band, as one
+// The PTP iteration (Sec. 4.2) over the sliding update band, as one
 // persistent cooperative kernel with the window control on the device.
 //
 // Iteration k recomputes every non-source vertex of the band
@@ -14,7 +14,7 @@
 // or entering the band, are recomputed.  Distances of skipped vertices that
 // changed in k-1 are copied forward so both buffers stay Jacobi-consistent.
 //
-// The update step (Sec. 2.2) is evaluated in FP32 in a form shifted by d1
+// The update step (Sec. 3.2) is evaluated in FP32 in a form shifted by d1
 // (the unknown is q = p - d1, a local quantity of the order of an edge), with
 // the discriminant written as det * (L - |d2-d1|) (L + |d2-d1|), L = |x2-x1|,
 // so neither the magnitude of d nor the front's alignment with an edge
@@ -43,7 +43,7 @@ namespace {
 //
 // PERM: the vertex data stay in the original order and band position p holds
 // vertex perm[p] (multi-source maps, where the paper also skips the
-// rearrangement, Sec. 4.1); otherwise position p is vertex p of the
+// rearrangement, Sec. 5.1); otherwise position p is vertex p of the
 // renumbered mesh.  LABELS: also carry a label per vertex (Voronoi regions).
 template <bool PERM, bool LABELS>
 __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(DistArgs a) {

@@ -5,7 +5,7 @@
 // tests once, and falls back to tested iterations if V_i has not converged,
 // so with predictions that do not exceed the plain method's counts the
 // result is the plain method's.  The paper notes that the iterations needed
-// grow as the toplesets diverge from the distance isocurves (Sec. 4.2); the
+// grow as the toplesets diverge from the distance isocurves (Sec. 5.2); the
 // features describe that per window.
 //
 // Window features (per topleset r, computed on the device):

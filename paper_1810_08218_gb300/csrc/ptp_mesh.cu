@@ -1,7 +1,7 @@
 // Mesh construction: validation, the vertex -> incident-triangle lists
 // ("corner lists"), the one-ring slots (fans in cyclic order), positions and
 // the bounding-box diameter.  The paper keeps the mesh as a compact half-edge
-// structure (Sec. 3.3); the update step only needs, per vertex, the
+// structure (Sec. 4.3); the update step only needs, per vertex, the
 // triangles around it, which is what this builds.
 #include <float.h>
 #include <math.h>

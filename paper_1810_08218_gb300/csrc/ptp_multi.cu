@@ -1,6 +1,6 @@
 // Multi-source maps in the original vertex order: geodesic Voronoi regions
-// and farthest-point sampling (Sec. 4.3, App. A).  The paper's multi-source
-// GPU runs skip the rearrangement of the vertices (Sec. 4.1); here the band
+// and farthest-point sampling (Sec. 5.3, App. A).  The paper's multi-source
+// GPU runs skip the rearrangement of the vertices (Sec. 5.1); here the band
 // is walked through the BFS queue instead, with every per-vertex array in the
 // original order, so a new source set costs one BFS and one window run and
 // no renumbering pass.

@@ -1,7 +1,7 @@
-// Toplesets (Sec. 3.1, Definition: V_0 = S, V_r = the not yet visited
+// Toplesets (Sec. 4.1, Definition: V_0 = S, V_r = the not yet visited
 // neighbours of V_{r-1}) by a level-synchronous breadth-first search inside
 // one thread-block cluster, and the renumbering of the mesh in topleset
-// order (Sec. 3.3): the BFS queue itself is the new vertex order, so V_r
+// order (Sec. 4.3): the BFS queue itself is the new vertex order, so V_r
 // occupies the index range [off[r], off[r+1]).  The renumbered mesh gets
 // one-ring slots (remapped from the mesh's), corner lists for the vertices
 // that have no slot, and the precomputed geometry of every ring triangle.

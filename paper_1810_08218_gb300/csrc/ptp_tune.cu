@@ -1,4 +1,4 @@
-// Launch-shape autotuner for the window kernels.  The iteration of Sec. 3.2
+// Launch-shape autotuner for the window kernels.  The iteration of Sec. 4.2
 // fixes what every launch computes (bands, tests, iterates); threads per CTA
 // and the number of CTAs only decide how the band's chunks are spread over
 // the GPU and how many CTAs meet at each iteration's grid barrier, and the

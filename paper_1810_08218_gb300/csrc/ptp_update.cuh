@@ -1,5 +1,5 @@
 // Device side of the window update shared by the single-map and batched
-// window kernels: the update step of Sec. 2.2 on one triangle, the fan
+// window kernels: the update step of Sec. 3.2 on one triangle, the fan
 // update of one vertex, work-skipping stamps and small reductions.  Every
 // definition lives in an unnamed namespace, so each translation unit that
 // includes this header gets its own copy.
@@ -81,7 +81,7 @@ __device__ __noinline__ float tri_solve_fp64(float3 e1f, float3 e2f, float d1f, 
     return fb;
 }
 
-// Update step (Sec. 2.2) for vertex x0 from triangle (x0, x1, x2), with
+// Update step (Sec. 3.2) for vertex x0 from triangle (x0, x1, x2), with
 // e1 = x1 - x0, e2 = x2 - x0, a1 = |e1|^2, l1 = |e1|, likewise a2, l2.
 // Returns the candidate distance: the planar solution when it exists and
 // satisfies the monotonicity condition Q X^T n < 0, else
@@ -121,7 +121,7 @@ __device__ __forceinline__ float tri_update(float3 e1, float3 e2, float d1, floa
 
 __device__ __forceinline__ float3 xyz(float4 p) { return make_float3(p.x, p.y, p.z); }
 
-// Update step (Sec. 2.2) for vertex u from ring triangle (u, x1, x2) with
+// Update step (Sec. 3.2) for vertex u from ring triangle (u, x1, x2) with
 // the triangle's precomputed geometry g = (b, L, alpha, beta) and edge
 // lengths l1 = |x1 - x_u|, l2 = |x2 - x_u|: q = delta * alpha + beta *
 // sqrt(disc) is the planar solution shifted by d1, kept when both
@@ -156,7 +156,7 @@ __device__ __noinline__ float tri_update_degenerate(const DistArgs &a, int u, in
 // two neighbours are both no closer than the current best are skipped: the
 // update never returns less than min(d1, d2).  With LABELS the new value
 // carries the label of the winning triangle's closer neighbour (Voronoi
-// regions, Sec. 4.3).
+// regions, Sec. 5.3).
 template <bool LABELS>
 __device__ __forceinline__ float update_ring(const DistArgs &a, int u, const int ids[PTP_RING], const float el[PTP_RING],
                                              const float4 g[PTP_TRI], int m, float best, const float *__restrict__ dp,

@@ -1,7 +1,7 @@
 """Seeded synthetic triangle meshes shaped like the paper's workloads.
 
-The paper (Sec. 4) measures on scanned models (bunny, armadillo, dragon, ...)
-and on a regular grid of 1,002,001 vertices (Sec. 4.2.2).  Those models are
+The paper (Sec. 5) measures on scanned models (bunny, armadillo, dragon, ...)
+and on a regular grid of 1,002,001 vertices (Sec. 5.2.2).  Those models are
 not available here, so these generators stand in for them: flat jittered
 grids (exact answer = Euclidean distance), subdivided spheres (exact answer =
 great-circle distance), noisy tori, bumpy spheres and fractal heightfields.

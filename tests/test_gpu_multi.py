@@ -1,6 +1,6 @@
 """Multi-source maps in the original vertex order (the path the paper uses for
-multi-source problems, Sec. 4.1): geodesic Voronoi regions and farthest-point
-sampling (Sec. 4.3, App. A), and the fixed-band variant (Sec. 5), against the
+multi-source problems, Sec. 5.1 and 6.1.5): geodesic Voronoi regions and farthest-point
+sampling (Sec. 5.3, App. A), and the fixed-band variant (Sec. 6.1), against the
 FP64 oracle."""
 import numpy as np
 import pytest

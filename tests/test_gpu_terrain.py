@@ -5,9 +5,9 @@ The oracle cannot run a whole map of this size in test time, and PTP
 values cannot be computed one vertex at a time, so the full-size run is
 checked through properties that hold at any size:
   * d(S) = 0 and every vertex is reached (the lattice is connected);
-  * fixpoint residual: run to the fixpoint (eps = 1e-7, Sec. 3.2's test with
+  * fixpoint residual: run to the fixpoint (eps = 1e-7, Sec. 4.2's test with
     a tiny threshold), then for sampled vertices apply the oracle's FP64
-    update step (Sec. 2.2) once more from the GPU's final neighbour values:
+    update step (Sec. 3.2) once more from the GPU's final neighbour values:
     it may lower d(v) by at most 1e-5 * diameter (the FP64 oracle's own
     residual on such meshes is below 1e-8 * diameter);
   * the paper-mode map (eps = 1e-3) lies above the fixpoint map (the

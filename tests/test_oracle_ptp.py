@@ -1,9 +1,9 @@
-"""Pins for the oracle's PTP iteration (Sec. 3.2) against what geometry and
+"""Pins for the oracle's PTP iteration (Sec. 4.2) against what geometry and
 the paper fix: exact planar fronts, Euclidean distance on flat meshes,
 great-circle distance on spheres, the Dijkstra edge-path upper bound, the
 order-independent fixpoint of the update operator, Jacobi invariance under
 relabelling, the band bounds of Eq. upper_band / lower_band, and the
-regular-grid error the paper prints (Sec. 4.2.2)."""
+regular-grid error the paper prints (Sec. 5.2.2)."""
 import math
 import os
 
@@ -67,13 +67,13 @@ def test_flat_grid_euclidean():
     dij = _mape(_dijkstra(V, F, S), ex)
     assert mape < 2.5
     assert dij > 4 * mape
-    assert r.K <= 2 * r.rho      # K about rho to 1.5 rho (Sec. 4.2)
+    assert r.K <= 2 * r.rho      # K about rho to 1.5 rho (Sec. 5.2)
 
 
 def test_regular_grid_error_decreases_and_matches_paper_scale():
     """Refining a regular grid lowers the error (a consistent scheme), and at
     the paper's 1,002,001-vertex size the error is of the order the paper
-    prints (Sec. 4.2.2); the paper's grid layout and source are not stated, so
+    prints (Sec. 5.2.2); the paper's grid layout and source are not stated, so
     a factor-of-three band around its value is accepted."""
     mapes = []
     for N in (65, 129, 257):
@@ -126,7 +126,7 @@ def test_fixpoint_is_order_independent(mesh):
 
 
 def test_jacobi_iterates_do_not_depend_on_labels():
-    """Each iterate d_k is a function of d_{k-1} alone (Sec. 3.2), so
+    """Each iterate d_k is a function of d_{k-1} alone (Sec. 4.2), so
     renumbering the vertices and reordering the faces must give the same
     iterates, band trace and result, bit for bit.  An in-place
     (Gauss-Seidel) sweep would depend on the numbering."""
@@ -184,7 +184,7 @@ def test_not_converged_cap():
 
 
 def test_fixed_band_variant_follows_its_rule():
-    """band_mode 1 (the fixed band of the complexity analysis, Sec. 5): the
+    """band_mode 1 (the fixed band of the complexity analysis, Sec. 6.1): the
     lower bound after iteration k is ceil(k/2) regardless of convergence, so
     the run takes 2*rho - 1 iterations and still reaches the Dijkstra-bounded
     distances."""

@@ -1,4 +1,4 @@
-"""Pins for the oracle's toplesets (Sec. 3.1, Definition of V_r and its
+"""Pins for the oracle's toplesets (Sec. 4.1, Definition of V_r and its
 partition properties): a library breadth-first search, the partition
 properties, and the 6r ring sizes of a valence-6 lattice."""
 import networkx as nx

@@ -1,4 +1,4 @@
-"""Pins for the oracle's per-triangle update step (Sec. 2.2, the planar
+"""Pins for the oracle's per-triangle update step (Sec. 3.2, the planar
 Kimmel-Sethian update with the monotonicity condition Q X^T n < 0 and the
 edge fallback).  Every expected value here comes from geometry, not from the
 oracle's own formula: a linear distance field is reproduced exactly when its
@@ -172,7 +172,7 @@ def test_invariances():
 def test_bounds():
     """The update never exceeds the edge paths; a planar solution in a
     triangle that is not obtuse at x0 arrives after both neighbours (the
-    monotonicity property of Sec. 2.2, which needs non-obtuse triangles)."""
+    monotonicity property of Sec. 3.2, which needs non-obtuse triangles)."""
     rng = np.random.default_rng(3)
     later = 0
     for _ in range(2000):
