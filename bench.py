@@ -39,7 +39,16 @@ WORKLOADS = {
                 "radial noise +-0.01r, one seeded source, eps=1e-3",
     "sphere_l7": "unit icosphere level 7 (163,842 vertices, 327,680 triangles), one seeded source, eps=1e-3",
     "flat65": "65x65 jittered unit square (4,225 vertices, 8,192 triangles), centre source, eps=1e-3",
+    "bumpy_l8_fps": "level-8 icosphere with 64 Gaussian bumps (655,362 vertices, 1,310,720 triangles): 1,000-sample "
+                    "farthest-point sampling from a seeded first vertex (999 multi-source maps, one captured CUDA "
+                    "graph relaunched per sample) plus a 64-seed geodesic Voronoi map from the first 64 samples, "
+                    "eps=1e-3",
+    "uneven_batch32": "32 meshes, even ones jittered unit squares and odd ones noisy tori, vertex counts log-uniform "
+                      "in 10k-2M (9,007,687 in total), one seeded source each, all maps in one persistent launch, "
+                      "eps=1e-3",
 }
+# workloads of several maps per step (their own step functions below)
+MULTI_MAP = ("bumpy_l8_fps", "uneven_batch32")
 # Algorithmic bytes per band vertex-update (the per-update traffic model): its
 # float4 position 16 B + d_{k-1} 4 B + d_k 4 B + row offset 4 B + six incident
 # pairs 48 B.  Neighbour data is counted once, under the neighbour's own update.
@@ -66,6 +75,26 @@ def _config(workload: str, world: int) -> dict:
             "step": "mesh_create + toplesets + distance (all hot-path stages)"}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest value of x over all ranks (x itself without a process
+    group); `device` holds the reduction tensor (CUDA for NCCL, CPU for gloo)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(total_ms: float, steps: int, world: int) -> tuple[float, float]:
+    """(ms per step, ms per map) for `world` independent replicas that each
+    ran `steps` maps in total_ms (the slowest rank's time): every rank's maps
+    count, so the whole job's time per map is total_ms / (steps * world)."""
+    return total_ms / steps, total_ms / (steps * world)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -77,10 +106,18 @@ def _peaks():
 
 
 def _kernel_source_hash() -> str:
+    """Hash of the window kernel's code (its sources without comments and
+    whitespace), so a recorded traffic figure is dropped when the code changes
+    but not when only a comment does."""
+    import re
+
     h = hashlib.sha256()
     for f in ("ptp_distance.cu", "ptp_update.cuh", "ptp_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1810_08218_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1810_08218_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("".join(text.split()).encode())
     return h.hexdigest()
 
 
@@ -282,13 +319,8 @@ def run_ours(args) -> None:
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
 
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    ms_per_step = total_ms / args.steps
-    value = total_ms / (args.steps * world)
+    total_ms = max_over_ranks(float(sum(step_ms)), dev)
+    ms_per_step, value = replica_throughput(total_ms, args.steps, world)
 
     # end to end through the public API with pinned host buffers: the H2D
     # copies of vertices, faces and sources and the D2H copy of the map are
@@ -306,11 +338,7 @@ def run_ours(args) -> None:
         dt = (time.perf_counter() - t) * 1e3
         if s >= args.warmup:
             e2e_ms.append(dt)
-    e2e_val = statistics.mean(e2e_ms)
-    if world > 1:
-        tt = torch.tensor([e2e_val], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_val = float(tt.item()) / world
+    e2e_val = max_over_ranks(statistics.mean(e2e_ms), dev) / world
 
     if rank == 0:
         peak, peak_kind = _peaks()
@@ -344,6 +372,209 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def _multi_line(args, metric_maps, step_ms, e2e_ms, h2d, d2h, launches, clocks, stats_ptp, extra, kern_ms=None):
+    """The JSON line of a several-maps workload (rank 0, N = 1)."""
+    peak, peak_kind = _peaks()
+    value = step_ms / metric_maps
+    t_ms = kern_ms if kern_ms is not None else step_ms
+    achieved = BYTES_PER_UPDATE * stats_ptp["band_updates"] / (t_ms * 1e-3) / 1e9
+    line = {
+        "metric": "ms per geodesic map", "value": round(value, 4), "unit": "ms", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(_config(args.workload, 1), maps_per_step=metric_maps),
+        "ptp": stats_ptp,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": peak_kind, "traffic": None,
+                     "scope": "window kernel" if kern_ms is not None else "whole step",
+                     "bytes_model": f"{BYTES_PER_UPDATE} B x {stats_ptp['band_updates']} band vertex-updates"},
+        "e2e": {"value": round(e2e_ms / metric_maps, 4), "unit": "ms", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    line.update(extra)
+    return line
+
+
+def _timed_steps(torch, stream, flush, step, n):
+    out = []
+    for _ in range(n):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def run_batch(args) -> None:
+    """32 uneven maps: all hot-path stages per map (mesh, toplesets), then
+    the batched window in one launch; beside it the same 32 maps one after
+    another through ptp_distance."""
+    import torch
+
+    from paper_1810_08218_gb300 import build, capi, meshes
+
+    rank, _, local = _dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    capi.load()
+    probs = meshes.uneven_batch(32, seed=0)
+    host = [(torch.from_numpy(np.ascontiguousarray(V, dtype=np.float32)).pin_memory(),
+             torch.from_numpy(F).pin_memory(), torch.from_numpy(S)) for V, F, S in probs]
+    dev = [(v.cuda(), f.cuda(), q.cuda()) for v, f, q in host]
+    sizes = [V.shape[0] for V, _, _ in probs]
+    outs = [torch.empty(n, dtype=torch.float32, device="cuda") for n in sizes]
+    houts = [torch.empty(n, dtype=torch.float32).pin_memory() for n in sizes]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    kb = torch.cuda.Event(enable_timing=True)
+    ke = torch.cuda.Event(enable_timing=True)
+    kb.record(stream)
+    ke.record(stream)
+    torch.cuda.synchronize()
+    params = capi.ptp_params_default(eps=1e-3)
+    params.ev_begin = kb.cuda_event
+    params.ev_end = ke.cuda_event
+    res = {}
+    # The meshes' toplesets are independent: each BFS occupies one 8-SM
+    # cluster, so they are built on 8 streams at once (host source lists, so
+    # no call waits for the device) and joined before the batch is created.
+    side = [torch.cuda.Stream() for _ in range(8)]
+    srcs = [np.ascontiguousarray(S, dtype=np.int32) for _, _, S in probs]
+
+    def batched(src=dev, out_host=False):
+        meshes_ = [capi.ptp_mesh_create(v, f) for v, f, _ in src]
+        ready = torch.cuda.Event()
+        ready.record(stream)
+        tops = []
+        for i, m in enumerate(meshes_):
+            ss = side[i % len(side)]
+            ss.wait_event(ready)
+            tops.append(capi.ptp_toplesets(m, srcs[i], stream=ss))
+        for ss in side:
+            ev = torch.cuda.Event()
+            ev.record(ss)
+            stream.wait_event(ev)
+        batch = capi.ptp_batch_create(tops, stream=stream)
+        res["st"] = capi.ptp_distance_batch(batch, params, outs)
+        capi.ptp_batch_destroy(batch)
+        if out_host:
+            for o, h in zip(outs, houts):
+                h.copy_(o, non_blocking=True)
+
+    seq_params = capi.ptp_params_default(eps=1e-3)
+
+    def sequential():
+        for (v, f, q), o in zip(dev, outs):
+            tops = capi.ptp_toplesets(capi.ptp_mesh_create(v, f), q)
+            capi.ptp_distance(tops, seq_params, o, stats=False)
+
+    for _ in range(args.warmup):
+        batched()
+        sequential()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = capi.ptp_kernel_launches()
+    kern, t_batch = [], []
+    for _ in range(args.steps):
+        t_batch += _timed_steps(torch, stream, flush, batched, 1)
+        kern.append(kb.elapsed_time(ke))
+    launches = capi.ptp_kernel_launches() - l0
+    clocks = sampler.stop()
+    t_seq = _timed_steps(torch, stream, flush, sequential, max(3, args.steps // 2))
+    # end to end: inputs from pinned host memory, maps back to pinned host memory
+    e2e = []
+    for s_ in range(args.warmup + min(args.steps, 10)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        batched(src=host, out_host=True)
+        torch.cuda.synchronize()
+        if s_ >= args.warmup:
+            e2e.append((time.perf_counter() - t) * 1e3)
+    st = res["st"]
+    stats_ptp = {"K_max": max(x["iterations"] for x in st), "K_sum": sum(x["iterations"] for x in st),
+                 "band_updates": sum(x["band_updates"] for x in st), "vertices": sum(sizes)}
+    line = _multi_line(args, 32, statistics.mean(t_batch), statistics.mean(e2e),
+                       sum(12 * V.shape[0] + 12 * F.shape[0] + 4 for V, F, _ in probs), 4 * sum(sizes), launches,
+                       clocks, stats_ptp,
+                       {"window_kernel_ms": round(statistics.mean(kern), 4),
+                        "sequential_ms_per_map": round(statistics.mean(t_seq) / 32, 4),
+                        "batch_speedup": round(statistics.mean(t_seq) / statistics.mean(t_batch), 3)},
+                       kern_ms=statistics.mean(kern))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_fps(args) -> None:
+    """1,000-sample farthest-point sampling (999 multi-source maps under one
+    captured CUDA graph) plus a 64-seed Voronoi map, mesh creation included."""
+    import torch
+
+    from paper_1810_08218_gb300 import build, capi, meshes
+
+    rank, _, local = _dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    capi.load()
+    V, F, S = meshes.bumpy_l8()
+    n = V.shape[0]
+    Vh = torch.from_numpy(np.ascontiguousarray(V, dtype=np.float32)).pin_memory()
+    Fh = torch.from_numpy(F).pin_memory()
+    Vt, Ft = Vh.cuda(), Fh.cuda()
+    ns, nv = 1000, 64
+    samples = torch.empty(ns, dtype=torch.int32, device="cuda")
+    d = torch.empty(n, dtype=torch.float32, device="cuda")
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
+    hs = torch.empty(ns, dtype=torch.int32).pin_memory()
+    hl = torch.empty(n, dtype=torch.int32).pin_memory()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    params = capi.ptp_params_default(eps=1e-3)
+    res = {}
+
+    def step(src=(Vt, Ft), out_host=False):
+        mesh = capi.ptp_mesh_create(*src)
+        res["fps"] = capi.ptp_fps(mesh, int(S[0]), ns, params, samples, use_graph=True)
+        res["vor"] = capi.ptp_voronoi(mesh, samples[:nv], params, d, lab)
+        if out_host:
+            hs.copy_(samples, non_blocking=True)
+            hl.copy_(lab, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = capi.ptp_kernel_launches()
+    t = _timed_steps(torch, stream, flush, step, args.steps)
+    launches = capi.ptp_kernel_launches() - l0
+    clocks = sampler.stop()
+    e2e = []
+    for s_ in range(args.warmup + min(args.steps, 5)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(src=(Vh, Fh), out_host=True)
+        torch.cuda.synchronize()
+        if s_ >= args.warmup:
+            e2e.append((time.perf_counter() - t0) * 1e3)
+    maps = (ns - 1) + 1
+    stats_ptp = {"fps_iterations": res["fps"]["iterations"], "band_updates": res["fps"]["band_updates"]
+                 + res["vor"]["band_updates"], "voronoi_K": res["vor"]["iterations"]}
+    line = _multi_line(args, maps, statistics.mean(t), statistics.mean(e2e), 12 * n + 12 * F.shape[0],
+                       4 * ns + 4 * n, launches, clocks, stats_ptp,
+                       {"fps_ms_per_sample": round(statistics.mean(t) / ns, 4)})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -356,7 +587,15 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload in MULTI_MAP:
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle timing is defined for the single-map "
+                              "workloads (torus_1m, sphere_l7, flat65)"}), flush=True)
+        else:
+            run_reference(args)
+    elif args.workload == "uneven_batch32":
+        run_batch(args)
+    elif args.workload == "bumpy_l8_fps":
+        run_fps(args)
     else:
         run_ours(args)
 

@@ -234,7 +234,11 @@ ptp_status ptp_distance_noalloc(ptp_toplesets_t *tops, const ptp_params *params,
  *
  * ptp_batch_create copies the count toplesets handles' renumbered layouts
  * into one concatenated device layout (208 bytes per vertex plus 8 per
- * corner); the handles may be destroyed afterwards.  All handles must live on
+ * corner) on `stream` and blocks until the copy is done; the handles may be
+ * destroyed afterwards.  Handles built on other streams (the toplesets of
+ * independent meshes can be built concurrently, each BFS occupying one
+ * 8-SM cluster) must be complete before the call: join those streams to
+ * `stream` first, or synchronise them.  All handles must live on
  * one device, with fewer than 2^26 vertices and 2^31 corners in total
  * (PTP_ERR_TOO_LARGE otherwise); count in [1, PTP_BATCH_MAX] (PTP_ERR_ARG).
  * The handle belongs to the caller: ptp_batch_destroy frees it, after its

@@ -470,6 +470,9 @@ extern "C" ptp_status ptp_batch_create(ptp_toplesets_t *const *tops, int32_t cou
         cbase += t->ncorner;
         ostart += t->n + 2;
     }
+    // wait for the copy, so the toplesets handles (possibly built on other
+    // streams) may be destroyed as soon as this returns
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         free_layout(L, s);
         cudaStreamSynchronize(s);
