@@ -193,6 +193,28 @@ ptp_status ptp_distance(ptp_toplesets_t *tops, const ptp_params *params, float *
                         ptp_stats *stats);
 
 /*
+ * ptp_distance_from_sources -- the whole map from a mesh and a source set in
+ * one launch, the toplesets being built while the iteration runs.
+ *
+ * Computes what ptp_toplesets followed by ptp_distance computes (Sec. 4.1,
+ * Sec. 4.2; the same iterates, hence bit-identical distances), but the BFS
+ * runs inside the window launch: a few CTAs expand the toplesets level by
+ * level while the others iterate, each iteration k waiting (on the device)
+ * only until V_0 .. V_{k+1} exist.  As in the paper's multi-source GPU runs
+ * (Sec. 5.1) the vertices are not rearranged: the band is walked through the
+ * BFS queue and every per-vertex array stays in the original order.
+ *  sources   [m] vertex indices (ptr_kind), m >= 1; repeats are ignored.
+ *  d_out     [n_verts] float32 DEVICE, original order; +inf if unreachable.
+ *  params    as ptp_distance; schedule must be NULL (PTP_ERR_ARG); the
+ *            events, when set, bracket the fused kernel.
+ * Asynchronous unless stats is non-NULL or the sources are DEVICE pointers
+ * (they are validated on the host).  Errors: PTP_ERR_ARG, PTP_ERR_INDEX, and
+ * the statuses of ptp_distance.  stats->rho is the number of toplesets.
+ */
+ptp_status ptp_distance_from_sources(ptp_mesh *mesh, const int32_t *sources, int32_t m, int ptr_kind,
+                                     const ptp_params *params, float *d_out, void *stream, ptp_stats *stats);
+
+/*
  * ptp_distance_noalloc -- ptp_distance for callers that may not allocate.
  * (An addition of this library; the paper has no counterpart.)
  *

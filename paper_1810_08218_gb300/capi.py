@@ -98,6 +98,7 @@ def load(path: str | None = None):
             "ptp_distance": (st, [P, P, P, P, P]),
             "ptp_last_stats": (st, [P, P, P]),
             "ptp_distance_noalloc": (st, [P, P, P, P, P]),
+            "ptp_distance_from_sources": (st, [P, P, i32, ctypes.c_int, P, P, P, P]),
             "ptp_batch_create": (st, [P, i32, P, P]),
             "ptp_distance_batch": (st, [P, P, P, P, P]),
             "ptp_batch_destroy": (st, [P]),
@@ -314,6 +315,19 @@ def ptp_distance_noalloc(tops: Toplesets, params: Params, d_out, stream=None, st
 
 
 PTP_NOALLOC_MAX_VERTS = 1048576
+
+
+def ptp_distance_from_sources(mesh: Mesh, sources, params: Params, d_out, stream=None, stats: bool = True,
+                              ok=(PTP_OK,)) -> dict | None:
+    """The map from a mesh and a source set in one fused launch (toplesets
+    built while the iteration runs); d_out float32 CUDA tensor [n]."""
+    ps, ks, keep = _array_arg(sources, np.int32)
+    st = Stats() if stats else None
+    code = load().ptp_distance_from_sources(mesh.handle, ps, int(np.prod(keep.shape)), ks, ctypes.byref(params),
+                                            ctypes.c_void_p(d_out.data_ptr()), _stream_ptr(stream),
+                                            ctypes.byref(st) if st is not None else None)
+    _check(code, "ptp_distance_from_sources", ok)
+    return st.as_dict() if st is not None else None
 
 
 PTP_BATCH_MAX = 32

@@ -103,7 +103,7 @@ __global__ void batch_copy(int N, int nb, int base, int cbase, int ncorner, int 
 }
 
 struct BatchArgs {
-    DistArgs a;         // n = N and the concatenated arrays, scratch and control block
+    DistArgs a;         // n = N and the concatenated arrays, scratch and control block (zeroed by the host)
     int count;
     const int *mapinfo;
     unsigned *fmask;    // [3] rotating per-iteration masks: bit b = some vertex of map b's V_i failed

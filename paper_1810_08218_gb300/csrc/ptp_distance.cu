@@ -31,6 +31,107 @@
 
 namespace {
 
+// BFS CTAs of the fused window launch: the toplesets (Sec. 4.1) level by
+// level into the queue.  Level L's entries queue[off[L], off[L+1]) are dealt
+// out one per producer thread and round (warps interleaved across the
+// producer CTAs); a lane loads its vertex's one-ring slot from the original
+// mesh and claims every neighbour still unvisited with atomicCAS (level -1 ->
+// L+1); a warp appends its claims to the queue with one atomicAdd on the
+// shared tail (with IPERM also recording each claimed vertex's position).
+// After the producers' own barrier one thread writes off[L+2] (the end of
+// V_{L+1}) and publishes it with a release store of ctrl->ready = L + 2
+// (PTP_LEVELS_DONE once a level comes out empty), which the window CTAs
+// acquire before they read those offsets and queue entries.  Producers
+// never wait for the window CTAs.
+template <bool IPERM>
+__device__ __noinline__ void bfs_producer(const DistArgs &a) {
+    const int P = a.producers;
+    const int n = a.n;
+    const int pid = (int)blockIdx.x - ((int)gridDim.x - P);
+    const int lane = threadIdx.x & 31;
+    const int pwarp = (int)(threadIdx.x >> 5) * P + pid;  // warps interleaved across the producer CTAs
+    const int nthr = (int)blockDim.x * P;
+    const int ptid = pwarp * 32 + lane;
+    unsigned long long prev_hi[2] = {0ull, 0ull};
+    int fbeg = 0;
+    int total = __ldcg(a.off + 1);  // V_0: the (unique) sources, already in the queue
+    for (int L = 0;; ++L) {
+        const int rounds = (total + nthr - 1) / nthr;
+        for (int r = 0; r < rounds; ++r) {  // warp-uniform
+            const int t = r * nthr + ptid;
+            const int u = t < total ? __ldcg(a.queue_w + fbeg + t) : -1;
+            const int m = u >= 0 ? __ldg(a.ometa + u) : PTP_META_GENERAL;
+            const int4 r0 = u >= 0 ? __ldg(a.oring + u) : make_int4(-1, -1, -1, -1);
+            const int4 r1 = u >= 0 ? __ldg(a.oring + n + u) : make_int4(-1, -1, -1, -1);
+            int w[PTP_RING];
+            unsigned claimed = 0;
+            if (u >= 0 && !(m & PTP_META_GENERAL)) {
+                const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+                const int cnt = m & PTP_META_CNT;
+                int old[PTP_RING];
+#pragma unroll
+                for (int q = 0; q < PTP_RING; ++q) {
+                    w[q] = ids[q];
+                    old[q] = q < cnt ? atomicCAS(a.level + ids[q], -1, L + 1) : 0;
+                }
+#pragma unroll
+                for (int q = 0; q < PTP_RING; ++q)
+                    if (q < cnt && old[q] == -1) claimed |= 1u << q;
+            } else if (u >= 0) {
+                // vertex without a ring slot: claim from its corner list
+                const int cb = __ldg(a.row + u), ce = __ldg(a.row + u + 1);
+                for (int c = cb; c < ce; ++c) {
+                    const int2 pr = __ldg(a.pairs + c);
+                    const int ww[2] = {pr.x, pr.y};
+                    for (int e = 0; e < 2; ++e)
+                        if (atomicCAS(a.level + ww[e], -1, L + 1) == -1) {
+                            const int at = atomicAdd(&a.ctrl->tail, 1);
+                            a.queue_w[at] = ww[e];
+                            if (IPERM) a.iperm[ww[e]] = at;
+                        }
+                }
+            }
+            // append the claimed ring neighbours, one atomic per warp
+            const int cntc = __popc(claimed);
+            int incl = cntc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+            if (wtot) {
+                int at = 0;
+                if (lane == 31) at = atomicAdd(&a.ctrl->tail, wtot);
+                at = __shfl_sync(0xffffffffu, at, 31) + incl - cntc;
+#pragma unroll
+                for (int q = 0; q < PTP_RING; ++q)
+                    if (claimed >> q & 1u) {
+                        a.queue_w[at] = w[q];
+                        if (IPERM) a.iperm[w[q]] = at;
+                        ++at;
+                    }
+            }
+        }
+        if (ptp_grid_sync(a.ctrl->pbar, L + 1, 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)P) < 0) return;
+        const int end = __ldcg(&a.ctrl->tail);  // final: every append precedes the barrier
+        const int next = end - (fbeg + total);
+        if (pid == 0 && threadIdx.x == 0) {
+            a.off_w[L + 2] = end;
+            if (next == 0) {
+                a.info_w[0] = L + 1;  // rho
+                a.info_w[1] = end;    // vertices reached
+                ptp_st_release_s32(&a.ctrl->ready, PTP_LEVELS_DONE);
+            } else {
+                ptp_st_release_s32(&a.ctrl->ready, L + 2);
+            }
+        }
+        if (next == 0) return;
+        fbeg += total;
+        total = next;
+    }
+}
+
 // The persistent window kernel.  Each iteration walks the band in chunks of
 // 32 consecutive band positions (coalesced), chunk c to warp c mod W with
 // the warps numbered across CTAs first, so even a narrow band spreads over
@@ -45,15 +146,29 @@ namespace {
 // vertex perm[p] (multi-source maps, where the paper also skips the
 // rearrangement, Sec. 5.1); otherwise position p is vertex p of the
 // renumbered mesh.  LABELS: also carry a label per vertex (Voronoi regions).
-template <bool PERM, bool LABELS>
+//
+// FUSED (with PERM): the last a.producers CTAs run the BFS (bfs_producer)
+// while the others iterate; before iteration k a window CTA waits until the
+// offsets it reads (up to off[k+2]) are published.  rho is unknown until the
+// BFS ends; until then every CTA has seen at least k+2 published levels, so
+// rho > k+1 and j_k = k, the same decision the known rho would give.
+template <bool PERM, bool LABELS, bool FUSED = false>
 __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(DistArgs a) {
-    const int rho = __ldcg(a.info);
+    if constexpr (FUSED) {
+        if ((int)blockIdx.x >= (int)gridDim.x - a.producers) {
+            bfs_producer<!PERM>(a);
+            return;
+        }
+    }
+    constexpr int RHO_UNKNOWN = 0x3fffffff;
+    const int ncta = FUSED ? (int)gridDim.x - a.producers : (int)gridDim.x;  // window CTAs
+    int rho = FUSED ? RHO_UNKNOWN : __ldcg(a.info);
     const int nsrc = __ldcg(a.off + 1);
-    const long long max_iter = a.max_iter > 0 ? a.max_iter : 8LL * rho + 64;
+    long long max_iter = a.max_iter > 0 ? a.max_iter : (FUSED ? (1LL << 40) : 8LL * rho + 64);
     const int lane = threadIdx.x & 31;
     const int wid = threadIdx.x >> 5;
-    const int gwarp = wid * gridDim.x + blockIdx.x;
-    const int nwarps = (blockDim.x >> 5) * gridDim.x;
+    const int gwarp = wid * ncta + blockIdx.x;
+    const int nwarps = (blockDim.x >> 5) * ncta;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned tot_active = 0, tot_changed = 0, nfp64 = 0;
     unsigned long long prev_hi[2] = {0ull, 0ull};
@@ -70,7 +185,99 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     __shared__ int s_nq;
 
     auto off_at = [&](int r) { return __ldcg(a.off + (r < rho ? r : rho)); };
-    auto vertex_at = [&](int pos) { return PERM ? __ldg(a.perm + pos) : pos; };
+    // the queue is written during a fused launch: read it through L2 there
+    auto vertex_at = [&](int pos) { return PERM ? (FUSED ? __ldcg(a.perm + pos) : __ldg(a.perm + pos)) : pos; };
+    // FUSED: wait until off[0 .. need] are published (or the BFS has ended);
+    // afterwards rho is set if known.  Called by every thread of the CTA.
+    // Returns false when a wait timed out or another CTA aborted.
+    __shared__ int s_wait[2];
+    int seen = 1;  // thread 0: levels seen published (off[0], off[1] are set before launch)
+    auto wait_levels = [&](int need) -> bool {
+        if (threadIdx.x == 0) {
+            int ok = 1;
+            if (seen < need) {
+                const long long t0 = clock64();
+                unsigned spins = 0;
+                while (true) {
+                    seen = ptp_ld_acquire_s32(&a.ctrl->ready);
+                    if (seen >= need) break;
+                    if ((++spins & 63u) == 0) {
+                        if (*(volatile int *)&a.ctrl->abort) { ok = 0; break; }
+                        if (clock64() - t0 > PTP_WAIT_CYCLES) {
+                            atomicExch(&a.ctrl->status, (int)PTP_ERR_TIMEOUT);
+                            atomicExch(&a.ctrl->abort, 1);
+                            ok = 0;
+                            break;
+                        }
+                    }
+                }
+            }
+            s_wait[0] = ok;
+            s_wait[1] = (ok && seen == PTP_LEVELS_DONE) ? __ldcg(a.info) : RHO_UNKNOWN;
+        }
+        __syncthreads();
+        const bool ok = s_wait[0] != 0;
+        if (s_wait[1] != RHO_UNKNOWN && rho == RHO_UNKNOWN) {
+            rho = s_wait[1];
+            if (a.max_iter <= 0) max_iter = 8LL * rho + 64;
+        }
+        __syncthreads();
+        return ok;
+    };
+    // what iteration k needs from the producers: offsets up to off[k+2]; in
+    // topleset order also the positions of V_{k+2}, since iteration k copies
+    // V_{k+1} (whose slots point into V_{k+2}) for iteration k+1
+    auto need_for = [](long long kk) { return PERM ? (int)kk + 2 : (int)kk + 3; };
+    // FUSED in topleset order: copy the vertices at positions [pb, pe) from
+    // the original mesh (slots remapped through iperm), 32-position chunks
+    // dealt to the warps from the last one down, so that in a narrow band
+    // the copying warps are not the ones with band chunks
+    auto copy_level = [&](int pb, int pe) {
+        if constexpr (FUSED && !PERM) {
+            const int n = a.n;
+            const int cb = pb & ~31;
+            const int rch = pe > cb ? (pe - cb + 31) >> 5 : 0;
+            for (int c = nwarps - 1 - gwarp; c < rch; c += nwarps) {
+                const int p = cb + c * 32 + lane;
+                if (p < pb || p >= pe) continue;
+                const int v = __ldcg(a.perm + p);
+                const int vm = __ldg(a.ometa + v);
+                const int4 v0 = __ldg(a.oring + v), v1 = __ldg(a.oring + n + v);
+                float4 g[PTP_TRI];
+#pragma unroll
+                for (int q = 0; q < PTP_TRI; ++q) g[q] = __ldg(a.otgeom + (size_t)q * n + v);
+                const float4 e0 = __ldg(a.oelen + v), e1 = __ldg(a.oelen + n + v), x = __ldg(a.opos + v);
+                const int vc = (vm & PTP_META_GENERAL) ? 0 : (vm & PTP_META_CNT);
+                auto mp = [&](int q, int id) { return q < vc ? __ldcg(a.iperm + id) : -1; };
+                a.ring_w[p] = make_int4(mp(0, v0.x), mp(1, v0.y), mp(2, v0.z), mp(3, v0.w));
+                a.ring_w[n + p] = make_int4(mp(4, v1.x), mp(5, v1.y), mp(6, v1.z), mp(7, v1.w));
+                a.meta_w[p] = vm;
+                a.pos_w[p] = x;
+#pragma unroll
+                for (int q = 0; q < PTP_TRI; ++q) a.tgeom_w[(size_t)q * n + p] = g[q];
+                a.elen_w[p] = e0;
+                a.elen_w[n + p] = e1;
+            }
+        }
+    };
+    // barrier epochs: the topleset-ordered fused run has one more barrier,
+    // after copying V_0 and V_1, so its iteration k uses epoch k + 1
+    constexpr long long EP0 = (FUSED && !PERM) ? 1 : 0;
+    if constexpr (FUSED) {
+        if (!wait_levels(need_for(1))) {
+            status = PTP_ERR_TIMEOUT;
+            k = 0;  // the loop below does not run
+        }
+        if constexpr (!PERM) {
+            if (k == 1) {
+                copy_level(0, off_at(2));  // V_0 and V_1
+                if (ptp_grid_sync(a.ctrl->bar, 1, 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)ncta) < 0) {
+                    status = PTP_ERR_TIMEOUT;
+                    k = 0;
+                }
+            }
+        }
+    }
     Band bd;  // iteration 1: i_0 = 0, j_1 = min(1, rho - 1)
     {
         const int j1 = rho > 1 ? 1 : 0;
@@ -81,7 +288,13 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         bd.hi = off_at(j1 + 1);
     }
 
-    for (; k <= max_iter; ++k) {
+    for (; k >= 1 && k <= max_iter; ++k) {
+        if constexpr (FUSED) {
+            if (!wait_levels(need_for(k))) {
+                status = PTP_ERR_TIMEOUT;
+                break;
+            }
+        }
         const int j = k < rho ? (int)k : rho - 1;
         const float *dp = (k & 1) ? a.d0 : a.d1;  // d_{k-1} lives in buffer (k-1) % 2
         float *dnx = (k & 1) ? a.d1 : a.d0;
@@ -138,14 +351,17 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         };
         // The geometry of every slot is loaded whatever the vertex's count:
         // every slot is written, and the loads need not wait for meta.
+        // (read through L2 when producers write them during this launch)
         auto load_slots = [&](int u, int &meta, int4 &r0, int4 &r1, float4 &l0, float4 &l1, float4 *g) {
-            meta = __ldg(a.meta + u);
-            r0 = __ldg(a.ring + u);
-            r1 = __ldg(a.ring + a.n + u);
-            l0 = __ldg(a.elen + u);
-            l1 = __ldg(a.elen + a.n + u);
+            constexpr bool CO = FUSED && !PERM;
+            meta = CO ? __ldcg(a.meta + u) : __ldg(a.meta + u);
+            r0 = CO ? __ldcg(a.ring + u) : __ldg(a.ring + u);
+            r1 = CO ? __ldcg(a.ring + a.n + u) : __ldg(a.ring + a.n + u);
+            l0 = CO ? __ldcg(a.elen + u) : __ldg(a.elen + u);
+            l1 = CO ? __ldcg(a.elen + a.n + u) : __ldg(a.elen + a.n + u);
 #pragma unroll
-            for (int t = 0; t < PTP_TRI; ++t) g[t] = __ldg(a.tgeom + (size_t)t * a.n + u);
+            for (int t = 0; t < PTP_TRI; ++t)
+                g[t] = CO ? __ldcg(a.tgeom + (size_t)t * a.n + u) : __ldg(a.tgeom + (size_t)t * a.n + u);
         };
 
         if (nchunks <= nwarps) {
@@ -245,6 +461,8 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                 __syncthreads();
             }
         }
+        // V_{k+1} into topleset order for the next iteration
+        if constexpr (FUSED && !PERM) copy_level(off_at((int)k + 1), off_at((int)k + 2));
         tot_active += n_active;
         tot_changed += n_changed;
 
@@ -284,7 +502,8 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         const int sched_next = (a.sched && i + 1 < rho) ? __ldcg(a.sched + i + 1) : 1;
 
         const int any = __syncthreads_or(notconv);
-        const long long failed = ptp_grid_sync(a.ctrl->bar, k, any ? 1u : 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi);
+        const long long failed =
+            ptp_grid_sync(a.ctrl->bar, k + EP0, any ? 1u : 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)ncta);
         if (failed < 0) {
             status = PTP_ERR_TIMEOUT;
             break;
@@ -423,7 +642,7 @@ ptp_status ptp_internal_window_multi(const ptp_mesh *mesh, ptp_multi_bufs *b, co
     if (per_sm < 1) return PTP_ERR_CUDA;
     int grid = per_sm * ptp_num_sms(dev);
     if (params->grid > 0 && params->grid < grid) grid = params->grid;
-    DistArgs a;
+    DistArgs a = {};
     a.n = n;
     a.pos = mesh->pos;
     a.ring = mesh->ring;
@@ -460,6 +679,158 @@ ptp_status ptp_internal_window_multi(const ptp_mesh *mesh, ptp_multi_bufs *b, co
 ptp_status ptp_internal_window_occupancy(int block, int *per_sm) {
     *per_sm = 0;
     PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, ptp_window<false, false>, block, 0));
+    return PTP_OK;
+}
+
+namespace {
+
+// V_0 of a fused launch: off[0..1], the BFS state the producers start from,
+// and (renumbering) the sources' positions.
+__global__ void fused_setup(ptp_ctrl *ctrl, int *off, const int *info, const int *queue, int *iperm) {
+    const int m0 = info[3];  // unique sources, queued by the seeding kernel
+    if (iperm)
+        for (int q = threadIdx.x; q < m0; q += blockDim.x) iperm[queue[q]] = q;
+    if (threadIdx.x != 0) return;
+    off[0] = 0;
+    off[1] = m0;
+    ctrl->tail = m0;
+    ctrl->ready = 1;
+}
+
+// Distances of a renumbered fused run, back to the original order:
+// d_out[v] = d_K[iperm[v]] for reached vertices, +inf for the others.
+__global__ void fused_gather(const ptp_ctrl *__restrict__ ctrl, int n, const int *__restrict__ level,
+                             const int *__restrict__ iperm, const float *__restrict__ d0, const float *__restrict__ d1,
+                             float *__restrict__ d_out) {
+    const float *d = (ctrl->iterations & 1) ? d1 : d0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        d_out[v] = level[v] >= 0 ? d[iperm[v]] : INF;
+}
+
+// Launch shape of a fused run: CTAs in all and how many run the BFS.  A
+// level's frontier grows like sqrt(n) on these meshes (a few thousand
+// vertices at a million), and one producer thread per frontier vertex keeps
+// a level to one round: 2 sqrt(n) threads, between 4096 and 8192, at most a
+// quarter of the grid (0 when the grid cannot split).
+ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, bool renum, bool labels, const void **fn,
+                       int *block, int *grid, int *producers) {
+    *fn = renum ? (const void *)ptp_window<false, false, true>
+                : labels ? (const void *)ptp_window<true, true, true> : (const void *)ptp_window<true, false, true>;
+    *block = window_block(params->block);
+    if (*block < 0) return PTP_ERR_ARG;
+    int per_sm = 0;
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, *fn, *block, 0));
+    if (per_sm < 1) return PTP_ERR_CUDA;
+    *grid = per_sm * ptp_num_sms(mesh->device);
+    if (params->grid > 0 && params->grid < *grid) *grid = params->grid;
+    double th = 2.0 * sqrt((double)mesh->n);
+    th = th < 4096.0 ? 4096.0 : (th > 8192.0 ? 8192.0 : th);
+    int p = ((int)th + *block - 1) / *block;
+    if (p > *grid / 4) p = *grid / 4;
+    *producers = p > 0 ? p : 0;
+    return PTP_OK;
+}
+
+}  // namespace
+
+int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params, bool renum) {
+    const void *fn;
+    int block, grid, producers;
+    if (fused_shape(mesh, params, renum, false, &fn, &block, &grid, &producers) != PTP_OK) return 0;
+    return producers;
+}
+
+ptp_status ptp_internal_fused_gather(const ptp_mesh *mesh, const ptp_multi_bufs *b, const ptp_renum_bufs *rb,
+                                     float *d_out, cudaStream_t s) {
+    fused_gather<<<blocks_for(b->n, 256, mesh->device), 256, 0, s>>>(b->ctrl, b->n, b->level, rb->iperm, b->d0, b->d1,
+                                                                     d_out);
+    ptp_count_launches(1);
+    PTP_TRY(cudaGetLastError());
+    return PTP_OK;
+}
+
+ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params, const int *src,
+                              const int *m_dev, int m_max, bool labels, const ptp_renum_bufs *rb, cudaStream_t s) {
+    const int n = b->n;
+    const int dev = mesh->device;
+    if (rb && labels) return PTP_ERR_ARG;
+    const void *fn;
+    int block, grid, producers;
+    PTP_CHECK(fused_shape(mesh, params, rb != nullptr, labels, &fn, &block, &grid, &producers));
+    if (producers < 1) {
+        // too few CTAs to split: the BFS first, then the window in the
+        // original order (the distances then follow the original numbering)
+        if (rb) return PTP_ERR_TOO_LARGE;
+        PTP_CHECK(ptp_internal_bfs(mesh, b, src, m_dev, m_max, s));
+        return ptp_internal_window_multi(mesh, b, params, src, m_dev, m_max, labels, s);
+    }
+    PTP_CHECK(ptp_internal_bfs_seed(mesh, b, src, m_dev, m_max, s));
+    PTP_TRY(cudaMemsetAsync(b->ctrl, 0, sizeof(ptp_ctrl), s));
+    fused_setup<<<1, 256, 0, s>>>(b->ctrl, b->off, b->info, b->queue, rb ? rb->iperm : nullptr);
+    if (rb) {
+        // distances by position: the sources are positions [0, off[1])
+        init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(b->off, n, b->d0, b->d1, b->nstamp, b->chg);
+        ptp_count_launches(2);
+    } else {
+        init_multi<<<blocks_for(n, 256, dev), 256, 0, s>>>(n, b->d0, b->d1, b->nstamp, b->chg,
+                                                            labels ? b->lab0 : nullptr, labels ? b->lab1 : nullptr);
+        seed_multi<<<blocks_for(m_max, 256, dev), 256, 0, s>>>(src, m_max, m_dev, b->d0, b->d1,
+                                                               labels ? b->lab0 : nullptr, labels ? b->lab1 : nullptr);
+        ptp_count_launches(3);
+    }
+    PTP_TRY(cudaGetLastError());
+    DistArgs a = {};
+    a.n = n;
+    a.pos = rb ? rb->pos : mesh->pos;
+    a.ring = rb ? rb->ring : mesh->ring;
+    a.tgeom = rb ? rb->tgeom : mesh->tgeom;
+    a.elen = rb ? rb->elen : mesh->elen;
+    a.meta = rb ? rb->meta : mesh->meta;
+    a.row = mesh->row;  // original corner lists (GENERAL vertices map through iperm with rb)
+    a.pairs = mesh->pairs;
+    a.off = b->off;
+    a.info = b->info;
+    a.d0 = b->d0;
+    a.d1 = b->d1;
+    a.nstamp = b->nstamp;
+    a.chg = b->chg;
+    a.ctrl = b->ctrl;
+    a.trace = (ptp_trace_rec *)params->trace;
+    a.trace_cap = params->trace ? params->trace_cap : 0;
+    a.eps = params->eps;
+    a.eps_abs = params->eps_abs;
+    a.max_iter = params->max_iter;
+    a.perm = b->queue;
+    a.lab0 = labels ? b->lab0 : nullptr;
+    a.lab1 = labels ? b->lab1 : nullptr;
+    a.band_mode = params->band_mode;
+    a.sched = nullptr;  // a schedule needs the whole toplesets first
+    a.producers = producers;
+    a.opos = mesh->pos;
+    a.oring = mesh->ring;
+    a.ometa = mesh->meta;
+    a.otgeom = mesh->tgeom;
+    a.oelen = mesh->elen;
+    if (rb) {
+        a.pos_w = rb->pos;
+        a.ring_w = rb->ring;
+        a.meta_w = rb->meta;
+        a.tgeom_w = rb->tgeom;
+        a.elen_w = rb->elen;
+        a.iperm = rb->iperm;
+        a.coherent = 1;
+    }
+    a.level = b->level;
+    a.queue_w = b->queue;
+    a.off_w = b->off;
+    a.info_w = b->info;
+    if (params->trace && params->trace_cap > 0)
+        PTP_TRY(cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s));
+    void *args[] = {(void *)&a};
+    if (params->ev_begin) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_begin, s));
+    PTP_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, s));
+    ptp_count_launches(1);
+    if (params->ev_end) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_end, s));
     return PTP_OK;
 }
 
@@ -522,7 +893,7 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
         int grid = per_sm * ptp_num_sms(dev);
         if (params->grid > 0 && params->grid < grid) grid = params->grid;
 
-        DistArgs a;
+        DistArgs a = {};
         a.n = (int)n;
         a.pos = t->pos;
         a.ring = t->ring;
@@ -675,7 +1046,7 @@ extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params 
     int grid = per_sm * ptp_num_sms(dev);
     if (params->grid > 0 && params->grid < grid) grid = params->grid;
 
-    DistArgs a;
+    DistArgs a = {};
     a.n = (int)n;
     a.pos = t->pos;
     a.ring = t->ring;

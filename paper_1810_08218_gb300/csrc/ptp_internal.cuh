@@ -51,7 +51,14 @@ struct ptp_ctrl {
     unsigned long long changed;  // updates that lowered d
     unsigned long long fp64;     // triangle solves taken in FP64
     long long checks;            // iterations that applied the test of Eq. lower_band
+    // BFS running inside the window launch (ptp_distance_from_sources):
+    unsigned long long pbar[2];  // barrier words of the BFS CTAs
+    int tail;                    // BFS queue length so far
+    int ready;                   // levels published: off[0 .. ready] and their queue entries
+                                 // are final (PTP_LEVELS_DONE once the BFS has ended)
 };
+
+#define PTP_LEVELS_DONE 0x7fffffff
 
 // One-ring slot layout of a renumbered vertex: its neighbours in cyclic
 // order in ring[2u], ring[2u+1] (8 int32, -1 padded).  meta[u] holds the
@@ -123,12 +130,42 @@ ptp_status ptp_internal_prepare();
 // (BFS queue order, no renumbering).  Resets the per-run BFS state itself.
 ptp_status ptp_internal_bfs(const ptp_mesh *mesh, ptp_multi_bufs *b, const int *src, const int *m_dev, int m_max,
                             cudaStream_t s);
+// Only the reset and V_0 of that BFS: level = -1 except the sources (0),
+// queue[0 .. info[3]) = the unique sources.
+ptp_status ptp_internal_bfs_seed(const ptp_mesh *mesh, ptp_multi_bufs *b, const int *src, const int *m_dev, int m_max,
+                                 cudaStream_t s);
 // Ring geometry of the mesh in the original numbering (cached in the mesh).
 ptp_status ptp_internal_mesh_geometry(ptp_mesh *mesh, cudaStream_t s);
 // Initialise distances (0 on the sources, which get labels 0..m-1) and run
 // the window kernel over b->queue in the original order.
 ptp_status ptp_internal_window_multi(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params,
                                      const int *src, const int *m_dev, int m_max, bool labels, cudaStream_t s);
+// The same map with the BFS running inside the window launch: seeds the
+// sources, initialises the distances and launches the fused window kernel,
+// whose last CTAs build the toplesets level by level into b->queue / off
+// while the others run the iteration as soon as the levels it needs exist.
+// Falls back to ptp_internal_bfs + ptp_internal_window_multi (or, with rb,
+// to the same steps in topleset order) when the grid is too small to split.
+// With `rb`, the producers also copy each level into topleset order (rb) one
+// level behind the BFS, and the window runs on that copy (positions; the
+// distances in b then follow the positions, rb->iperm maps back); without
+// it the window walks the queue over the original order (labels allowed).
+struct ptp_renum_bufs {
+    float4 *pos;    // [n]
+    int4 *ring;     // [2 n]
+    int *meta;      // [n]
+    float4 *tgeom;  // [PTP_TRI n]
+    float4 *elen;   // [2 n]
+    int *iperm;     // [n] original vertex -> position
+};
+ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params, const int *src,
+                              const int *m_dev, int m_max, bool labels, const ptp_renum_bufs *rb, cudaStream_t s);
+// Producer CTAs a fused launch with these params would get (0: the grid is
+// too small to split, and ptp_internal_fused would run the two steps).
+int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params, bool renum);
+// d_out (original order) from a run with rb.
+ptp_status ptp_internal_fused_gather(const ptp_mesh *mesh, const ptp_multi_bufs *b, const ptp_renum_bufs *rb,
+                                     float *d_out, cudaStream_t s);
 // The final distance (and label) buffer of the last window run in b.
 __host__ __device__ inline int ptp_final_buffer(long long iterations) { return (int)(iterations & 1); }
 
@@ -164,6 +201,16 @@ __device__ __forceinline__ unsigned long long ptp_ld_acquire_u64(const unsigned 
     return v;
 }
 
+__device__ __forceinline__ int ptp_ld_acquire_s32(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void ptp_st_release_s32(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long ptp_atom_add_release_u64(unsigned long long *p, unsigned long long v) {
     unsigned long long old;
     asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
@@ -180,14 +227,16 @@ __device__ __forceinline__ unsigned long long ptp_atom_add_release_u64(unsigned 
 // carries those previous high halves.  Returns the sum, or -1 when the wait
 // timed out here (PTP_ERR_TIMEOUT is written to *status) or another CTA
 // flagged an abort; the caller must then leave its loop.  epoch starts at 1.
+// `parts` is the number of CTAs that take part (0: the whole grid).
 __device__ __forceinline__ long long ptp_grid_sync(unsigned long long *words, long long epoch, unsigned value,
-                                                   int *abort_flag, int *status, unsigned long long *prev_hi) {
+                                                   int *abort_flag, int *status, unsigned long long *prev_hi,
+                                                   unsigned parts = 0) {
     __shared__ long long result_s;
     __syncthreads();
     if (threadIdx.x == 0) {
         const int w = (int)(epoch & 1);
         unsigned long long *word = words + w;
-        const unsigned target = (unsigned)((epoch + 1) >> 1) * gridDim.x;
+        const unsigned target = (unsigned)((epoch + 1) >> 1) * (parts ? parts : gridDim.x);
         const unsigned long long add = 1ull + ((unsigned long long)value << 32);
         unsigned long long v = ptp_atom_add_release_u64(word, add) + add;
         long long res = 0;

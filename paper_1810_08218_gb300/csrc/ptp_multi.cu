@@ -170,6 +170,75 @@ void fill_stats(ptp_stats *st, const ptp_ctrl &h, int rho) {
 
 }  // namespace
 
+extern "C" ptp_status ptp_distance_from_sources(ptp_mesh *mesh, const int32_t *sources, int32_t m, int ptr_kind,
+                                               const ptp_params *params, float *d_out, void *stream,
+                                               ptp_stats *stats) {
+    if (!mesh || !sources || m < 1 || !d_out || (ptr_kind != PTP_HOST && ptr_kind != PTP_DEVICE)) return PTP_ERR_ARG;
+    PTP_CHECK(check_params(params));
+    if (params->schedule) return PTP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)mesh->n;
+    std::vector<int32_t> h((size_t)m);
+    if (ptr_kind == PTP_DEVICE) {
+        PTP_TRY(cudaMemcpyAsync(h.data(), sources, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, s));
+        PTP_TRY(cudaStreamSynchronize(s));
+    } else {
+        memcpy(h.data(), sources, sizeof(int32_t) * m);
+    }
+    for (int32_t q = 0; q < m; ++q)
+        if (h[q] < 0 || h[q] >= n) return PTP_ERR_INDEX;
+    PTP_CHECK(ptp_internal_prepare());
+    PTP_CHECK(ptp_internal_mesh_geometry(mesh, s));
+    MultiAlloc ma;
+    void *src_v = nullptr;
+    PTP_CHECK(ma.alloc(n, false, sizeof(int) * (size_t)m, &src_v, s));
+    int *src = (int *)src_v;
+    PTP_TRY(cudaMemcpyAsync(src, h.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+    if (ptp_internal_fused_producers(mesh, params, true) > 0) {
+        // topleset-ordered copy written by the producers (208 B per vertex)
+        const size_t N = (size_t)n;
+        const size_t parts[] = {sizeof(float4) * N, sizeof(int4) * 2 * N, sizeof(int) * N,
+                                sizeof(float4) * PTP_TRI * N, sizeof(float4) * 2 * N, sizeof(int) * N};
+        size_t bytes = 0;
+        for (size_t z : parts) bytes += (z + 255) & ~(size_t)255;
+        char *base = nullptr;
+        PTP_TRY(cudaMallocAsync((void **)&base, bytes, s));
+        ptp_renum_bufs rb;
+        char *q = base;
+        auto take = [&](size_t z) {
+            char *r = q;
+            q += (z + 255) & ~(size_t)255;
+            return (void *)r;
+        };
+        rb.pos = (float4 *)take(parts[0]);
+        rb.ring = (int4 *)take(parts[1]);
+        rb.meta = (int *)take(parts[2]);
+        rb.tgeom = (float4 *)take(parts[3]);
+        rb.elen = (float4 *)take(parts[4]);
+        rb.iperm = (int *)take(parts[5]);
+        ptp_status st = ptp_internal_fused(mesh, &ma.b, params, src, nullptr, m, false, &rb, s);
+        if (st == PTP_OK) st = ptp_internal_fused_gather(mesh, &ma.b, &rb, d_out, s);
+        cudaFreeAsync(base, s);
+        PTP_CHECK(st);
+    } else {
+        // too few CTAs to split the launch: BFS, then the window in the original order
+        PTP_CHECK(ptp_internal_bfs(mesh, &ma.b, src, nullptr, m, s));
+        PTP_CHECK(ptp_internal_window_multi(mesh, &ma.b, params, src, nullptr, m, false, s));
+        multi_out<<<blocks_for(n, 256, mesh->device), 256, 0, s>>>(ma.b.ctrl, n, ma.b.d0, ma.b.d1, nullptr, nullptr,
+                                                                    d_out, nullptr);
+        ptp_count_launches(1);
+        PTP_TRY(cudaGetLastError());
+    }
+    if (!stats) return PTP_OK;
+    ptp_ctrl hc;
+    int info[4];
+    PTP_TRY(cudaMemcpyAsync(&hc, ma.b.ctrl, sizeof(ptp_ctrl), cudaMemcpyDeviceToHost, s));
+    PTP_TRY(cudaMemcpyAsync(info, ma.b.info, sizeof(info), cudaMemcpyDeviceToHost, s));
+    PTP_TRY(cudaStreamSynchronize(s));
+    fill_stats(stats, hc, info[0]);
+    return (ptp_status)hc.status;
+}
+
 extern "C" ptp_status ptp_voronoi(ptp_mesh *mesh, const int32_t *seeds, int32_t m, int ptr_kind,
                                   const ptp_params *params, float *d_out, int32_t *label_out, void *stream,
                                   ptp_stats *stats) {

@@ -327,17 +327,26 @@ ptp_status ptp_internal_prepare() {
     return PTP_OK;
 }
 
-ptp_status ptp_internal_bfs(const ptp_mesh *mesh, ptp_multi_bufs *b, const int *src, const int *m_dev, int m_max,
-                            cudaStream_t s) {
+ptp_status ptp_internal_bfs_seed(const ptp_mesh *mesh, ptp_multi_bufs *b, const int *src, const int *m_dev, int m_max,
+                                 cudaStream_t s) {
     const int n = b->n;
     PTP_TRY(cudaMemsetAsync(b->level, 0xFF, sizeof(int) * n, s));
     PTP_TRY(cudaMemsetAsync(b->info, 0, sizeof(int) * 4, s));
     PTP_TRY(cudaMemsetAsync(b->cnt, 0, sizeof(int) * 16, s));
     bfs_seed<<<blocks_for(m_max, 256, mesh->device), 256, 0, s>>>(src, m_max, m_dev, b->level, b->queue, b->info);
+    ptp_count_launches(1);
+    PTP_TRY(cudaGetLastError());
+    return PTP_OK;
+}
+
+ptp_status ptp_internal_bfs(const ptp_mesh *mesh, ptp_multi_bufs *b, const int *src, const int *m_dev, int m_max,
+                            cudaStream_t s) {
+    const int n = b->n;
+    PTP_CHECK(ptp_internal_bfs_seed(mesh, b, src, m_dev, m_max, s));
     bfs_cluster<<<BC_CLUSTER, BC_THREADS, sizeof(int) * 2 * BC_CAP, s>>>(mesh->ring, mesh->meta, mesh->row, mesh->pairs,
                                                                          n, b->level, b->queue, b->off, b->info, b->spill,
                                                                          b->cnt);
-    ptp_count_launches(2);
+    ptp_count_launches(1);
     PTP_TRY(cudaGetLastError());
     return PTP_OK;
 }

@@ -43,6 +43,28 @@ struct DistArgs {
     int *lab1;
     int band_mode;    // 0: Eq. lower_band; 1: fixed band, i_k = ceil(k / 2)
     const int *sched; // learned schedule per topleset, or NULL
+    // BFS inside the launch (fused window): the last `producers` CTAs
+    int producers;
+    int *level;       // [n] BFS level, -1 unvisited
+    int *queue_w;     // the BFS queue (= perm), written by the producers
+    int *off_w;       // topleset offsets, written by the producers
+    int *info_w;      // [0] rho, [1] vertices reached
+    // ... reading the mesh in its original numbering
+    const float4 *opos;
+    const int4 *oring;
+    const int *ometa;
+    const float4 *otgeom;
+    const float4 *oelen;
+    // ... and, when they also renumber, writing the topleset-ordered copies
+    // that pos / ring / meta / tgeom / elen point to, plus the map
+    // original -> position (then row / pairs are the original corner lists)
+    float4 *pos_w;
+    int4 *ring_w;
+    int *meta_w;
+    float4 *tgeom_w;
+    float4 *elen_w;
+    int *iperm;
+    int coherent;     // the renumbered arrays are written during the launch: load them through L2
 };
 
 __device__ __forceinline__ float fsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
@@ -146,8 +168,9 @@ __device__ __noinline__ float tri_update_degenerate(const DistArgs &a, int u, in
                                                     float l1, float l2) {
     const float fb = fminf(d1 + l1, d2 + l2);
     if (!(fmaxf(d1, d2) < INF)) return fb;
-    const float3 x0 = xyz(__ldg(a.pos + u));
-    return tri_solve_fp64(sub3(xyz(__ldg(a.pos + id1)), x0), sub3(xyz(__ldg(a.pos + id2)), x0), d1, d2, fb);
+    auto ld = [&](int x) { return xyz(a.coherent ? __ldcg(a.pos + x) : __ldg(a.pos + x)); };
+    const float3 x0 = ld(u);
+    return tri_solve_fp64(sub3(ld(id1), x0), sub3(ld(id2), x0), d1, d2, fb);
 }
 
 // New value of a ring-slot vertex: min of the old value and the update over
@@ -186,29 +209,38 @@ __device__ __forceinline__ float update_ring(const DistArgs &a, int u, const int
 // New value of a GENERAL vertex from its corner list.
 __device__ __noinline__ float update_general(const DistArgs &a, int u, float best, const float *__restrict__ dp,
                                              const int *__restrict__ lp, int *label, unsigned &nfp64) {
-    const float3 x0 = xyz(__ldg(a.pos + u));
-    const int cb = __ldg(a.row + u), ce = __ldg(a.row + u + 1);
+    // With a.iperm (fused, renumbered) the corner lists are the original ones:
+    // vertex u is original vertex perm[u] and a corner's ids map through iperm.
+    const bool fmap = a.iperm != nullptr;
+    const int v = fmap ? __ldcg(a.perm + u) : u;
+    const float3 x0 = xyz(fmap ? __ldg(a.opos + v) : __ldg(a.pos + u));
+    const int cb = __ldg(a.row + v), ce = __ldg(a.row + v + 1);
     for (int c = cb; c < ce; ++c) {
         const int2 pr = __ldg(a.pairs + c);
-        const float d1 = __ldcg(dp + pr.x), d2 = __ldcg(dp + pr.y);
+        const int p1 = fmap ? __ldcg(a.iperm + pr.x) : pr.x, p2 = fmap ? __ldcg(a.iperm + pr.y) : pr.y;
+        const float d1 = __ldcg(dp + p1), d2 = __ldcg(dp + p2);
         if (!(fminf(d1, d2) < best)) continue;
-        const float3 e1 = sub3(xyz(__ldg(a.pos + pr.x)), x0), e2 = sub3(xyz(__ldg(a.pos + pr.y)), x0);
+        const float3 x1 = xyz(fmap ? __ldg(a.opos + pr.x) : __ldg(a.pos + pr.x));
+        const float3 x2 = xyz(fmap ? __ldg(a.opos + pr.y) : __ldg(a.pos + pr.y));
+        const float3 e1 = sub3(x1, x0), e2 = sub3(x2, x0);
         const float a1 = dot3(e1, e1), a2 = dot3(e2, e2);
         const float cand = tri_update(e1, e2, d1, d2, a1, fsqrt(a1), a2, fsqrt(a2), nfp64);
         if (cand < best) {
             best = cand;
-            if (label) *label = __ldcg(lp + (d1 <= d2 ? pr.x : pr.y));
+            if (label) *label = __ldcg(lp + (d1 <= d2 ? p1 : p2));
         }
     }
     return best;
 }
 
 __device__ __noinline__ void stamp_general(const DistArgs &a, int u, int k) {
-    const int cb = __ldg(a.row + u), ce = __ldg(a.row + u + 1);
+    const bool fmap = a.iperm != nullptr;
+    const int v = fmap ? __ldcg(a.perm + u) : u;
+    const int cb = __ldg(a.row + v), ce = __ldg(a.row + v + 1);
     for (int c = cb; c < ce; ++c) {
         const int2 pr = __ldg(a.pairs + c);
-        a.nstamp[pr.x] = k;
-        a.nstamp[pr.y] = k;
+        a.nstamp[fmap ? __ldcg(a.iperm + pr.x) : pr.x] = k;
+        a.nstamp[fmap ? __ldcg(a.iperm + pr.y) : pr.y] = k;
     }
 }
 
