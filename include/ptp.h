@@ -390,7 +390,10 @@ ptp_status ptp_mlp_to_half(const float *w, uint16_t *w_half, void *stream);
 ptp_status ptp_last_stats(ptp_toplesets_t *tops, void *stream, ptp_stats *stats);
 
 /*
- * All stages in one call: mesh, toplesets, distance, then release.
+ * All stages in one call: mesh, then the map with the toplesets built inside
+ * the window launch (ptp_distance_from_sources; with a schedule,
+ * ptp_toplesets + ptp_distance), then release.  The distances are those of
+ * ptp_toplesets + ptp_distance.
  *  ptr_kind applies to xyz, faces, sources AND d_out (host d_out is filled
  *  by a device-to-host copy before returning).  Blocks on `stream`.
  */

@@ -949,31 +949,37 @@ extern "C" ptp_status ptp_geodesic(const float *xyz, int64_t n_verts, const int3
     cudaStream_t s = (cudaStream_t)stream;
     ptp_mesh *mesh = nullptr;
     PTP_CHECK(ptp_mesh_create(xyz, n_verts, faces, n_faces, ptr_kind, stream, &mesh));
-    ptp_toplesets_t *tops = nullptr;
-    ptp_status st = ptp_toplesets(mesh, sources, m, ptr_kind, stream, &tops);
-    if (st != PTP_OK) {
-        ptp_mesh_destroy(mesh);
-        return st;
-    }
     float *dev_out = d_out;
     if (ptr_kind == PTP_HOST) {
         cudaError_t ce = cudaMallocAsync((void **)&dev_out, sizeof(float) * n_verts, s);
         if (ce != cudaSuccess) {
-            ptp_toplesets_destroy(tops);
             ptp_mesh_destroy(mesh);
             return ptp_internal_cuda_status(ce);
         }
     }
     ptp_stats local;
-    st = ptp_distance(tops, params, dev_out, stream, &local);
+    ptp_status st;
+    if (!params->schedule) {
+        // toplesets built inside the window launch
+        st = ptp_distance_from_sources(mesh, sources, m, ptr_kind, params, dev_out, stream, &local);
+    } else {
+        // a learned schedule needs the whole toplesets first
+        ptp_toplesets_t *tops = nullptr;
+        st = ptp_toplesets(mesh, sources, m, ptr_kind, stream, &tops);
+        if (st == PTP_OK) {
+            st = ptp_distance(tops, params, dev_out, stream, &local);
+            ptp_toplesets_destroy(tops);
+        }
+    }
     if (ptr_kind == PTP_HOST) {
-        cudaError_t ce = cudaMemcpyAsync(d_out, dev_out, sizeof(float) * n_verts, cudaMemcpyDeviceToHost, s);
+        cudaError_t ce = cudaSuccess;
+        if (st == PTP_OK || st == PTP_ERR_NOT_CONVERGED)
+            ce = cudaMemcpyAsync(d_out, dev_out, sizeof(float) * n_verts, cudaMemcpyDeviceToHost, s);
         cudaFreeAsync(dev_out, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess && (st == PTP_OK || st == PTP_ERR_NOT_CONVERGED)) st = ptp_internal_cuda_status(ce);
     }
-    if (stats) *stats = local;
-    ptp_toplesets_destroy(tops);
+    if (stats && (st == PTP_OK || st == PTP_ERR_NOT_CONVERGED)) *stats = local;
     ptp_mesh_destroy(mesh);
     return st;
 }
