@@ -149,6 +149,40 @@ struct MultiAlloc {
     }
 };
 
+// The topleset-ordered copy a fused run writes (ptp_renum_bufs), in one
+// stream-ordered allocation freed with the object.
+struct RenumAlloc {
+    ptp_renum_bufs rb;
+    void *base = nullptr;
+    cudaStream_t s = nullptr;
+    ptp_status alloc(int n, cudaStream_t st) {
+        s = st;
+        const size_t N = (size_t)n;
+        const size_t parts[] = {sizeof(float4) * N, sizeof(int4) * 2 * N, sizeof(int) * N,
+                                sizeof(float4) * PTP_TRI * N, sizeof(float4) * 2 * N, sizeof(int) * N};
+        size_t bytes = 0;
+        for (size_t z : parts) bytes += (z + 255) & ~(size_t)255;
+        PTP_TRY(cudaMallocAsync(&base, bytes, st));
+        char *q = (char *)base;
+        int i = 0;
+        auto take = [&]() {
+            char *r = q;
+            q += (parts[i++] + 255) & ~(size_t)255;
+            return (void *)r;
+        };
+        rb.pos = (float4 *)take();
+        rb.ring = (int4 *)take();
+        rb.meta = (int *)take();
+        rb.tgeom = (float4 *)take();
+        rb.elen = (float4 *)take();
+        rb.iperm = (int *)take();
+        return PTP_OK;
+    }
+    ~RenumAlloc() {
+        if (base) cudaFreeAsync(base, s);
+    }
+};
+
 ptp_status check_params(const ptp_params *p) {
     if (!p) return PTP_ERR_ARG;
     if (!(p->eps >= 0.0) || !(p->eps_abs >= 0.0) || p->max_iter < 0 || p->trace_cap < 0) return PTP_ERR_ARG;
@@ -195,31 +229,11 @@ extern "C" ptp_status ptp_distance_from_sources(ptp_mesh *mesh, const int32_t *s
     int *src = (int *)src_v;
     PTP_TRY(cudaMemcpyAsync(src, h.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
     if (ptp_internal_fused_producers(mesh, params, true) > 0) {
-        // topleset-ordered copy written by the producers (208 B per vertex)
-        const size_t N = (size_t)n;
-        const size_t parts[] = {sizeof(float4) * N, sizeof(int4) * 2 * N, sizeof(int) * N,
-                                sizeof(float4) * PTP_TRI * N, sizeof(float4) * 2 * N, sizeof(int) * N};
-        size_t bytes = 0;
-        for (size_t z : parts) bytes += (z + 255) & ~(size_t)255;
-        char *base = nullptr;
-        PTP_TRY(cudaMallocAsync((void **)&base, bytes, s));
-        ptp_renum_bufs rb;
-        char *q = base;
-        auto take = [&](size_t z) {
-            char *r = q;
-            q += (z + 255) & ~(size_t)255;
-            return (void *)r;
-        };
-        rb.pos = (float4 *)take(parts[0]);
-        rb.ring = (int4 *)take(parts[1]);
-        rb.meta = (int *)take(parts[2]);
-        rb.tgeom = (float4 *)take(parts[3]);
-        rb.elen = (float4 *)take(parts[4]);
-        rb.iperm = (int *)take(parts[5]);
-        ptp_status st = ptp_internal_fused(mesh, &ma.b, params, src, nullptr, m, false, &rb, s);
-        if (st == PTP_OK) st = ptp_internal_fused_gather(mesh, &ma.b, &rb, d_out, s);
-        cudaFreeAsync(base, s);
-        PTP_CHECK(st);
+        // topleset-ordered copy written during the launch (200 B per vertex)
+        RenumAlloc ra;
+        PTP_CHECK(ra.alloc(n, s));
+        PTP_CHECK(ptp_internal_fused(mesh, &ma.b, params, src, nullptr, m, false, &ra.rb, s));
+        PTP_CHECK(ptp_internal_fused_gather(mesh, &ma.b, &ra.rb, d_out, s));
     } else {
         // too few CTAs to split the launch: BFS, then the window in the original order
         PTP_CHECK(ptp_internal_bfs(mesh, &ma.b, src, nullptr, m, s));
@@ -282,6 +296,9 @@ extern "C" ptp_status ptp_voronoi(ptp_mesh *mesh, const int32_t *seeds, int32_t 
 namespace {
 
 // One sampling step: map from samples[0 .. *m_dev), then append its argmax.
+// (A sampling map recomputes the whole mesh from the new source set, so its
+// cost is the window's wide iterations, not the BFS: the two steps in the
+// original order serve it as well as the fused launch.)
 ptp_status fps_step(ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params, int *samples, int *m_dev,
                     int n_samples, FpsAccum *acc, cudaStream_t s) {
     const int n = b->n;
@@ -314,6 +331,7 @@ extern "C" ptp_status ptp_fps(ptp_mesh *mesh, int32_t first, int32_t n_samples, 
     PTP_CHECK(ma.alloc(n, false, sizeof(FpsAccum) + 256 + sizeof(int) * 4, &ex, us));
     FpsAccum *acc = (FpsAccum *)ex;
     int *m_dev = (int *)((char *)ex + ((sizeof(FpsAccum) + 255) & ~(size_t)255));
+
     fps_init<<<1, 32, 0, us>>>(acc, samples_out, m_dev, first);
     ptp_count_launches(1);
     PTP_TRY(cudaGetLastError());
@@ -331,16 +349,19 @@ extern "C" ptp_status ptp_fps(ptp_mesh *mesh, int32_t first, int32_t n_samples, 
             if (e == cudaSuccess) e = cudaEventRecord(ev, us);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
             if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            int64_t per_step = 0;
             if (e == cudaSuccess) {
+                const int64_t c0 = ptp_kernel_launches();
                 st = fps_step(mesh, &ma.b, &p, samples_out, m_dev, n_samples, acc, cs);
+                per_step = ptp_kernel_launches() - c0;
                 const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
                 if (st == PTP_OK && e2 != cudaSuccess) e = e2;
             }
-            ptp_count_launches(-7);  // recorded into the graph, not launched
+            ptp_count_launches((int)-per_step);  // recorded into the graph, not launched
             if (st == PTP_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
             for (int i = 1; st == PTP_OK && e == cudaSuccess && i < n_samples; ++i) {
                 e = cudaGraphLaunch(exec, cs);
-                ptp_count_launches(7);  // the kernels captured in one step
+                ptp_count_launches((int)per_step);  // the kernels captured in one step
             }
             if (e == cudaSuccess) e = cudaEventRecord(ev, cs);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(us, ev, 0);
@@ -363,8 +384,9 @@ extern "C" ptp_status ptp_fps(ptp_mesh *mesh, int32_t first, int32_t n_samples, 
         PTP_CHECK(ptp_internal_window_multi(mesh, &ma.b, &p, samples_out, m_dev, n_samples, false, us));
         multi_out<<<blocks_for(n, 256, mesh->device), 256, 0, us>>>(ma.b.ctrl, n, ma.b.d0, ma.b.d1, nullptr, nullptr,
                                                                      d_out, nullptr);
+        ptp_count_launches(1);
         fps_fold<<<1, 32, 0, us>>>(acc, ma.b.ctrl, ma.b.info);
-        ptp_count_launches(2);
+        ptp_count_launches(1);
         PTP_TRY(cudaGetLastError());
     }
     if (!stats) return PTP_OK;
