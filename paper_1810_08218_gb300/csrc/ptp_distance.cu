@@ -37,13 +37,12 @@ namespace {
 // producer CTAs); a lane loads its vertex's one-ring slot from the original
 // mesh and claims every neighbour still unvisited with atomicCAS (level -1 ->
 // L+1); a warp appends its claims to the queue with one atomicAdd on the
-// shared tail (with IPERM also recording each claimed vertex's position).
+// shared tail, recording each claimed vertex's position in iperm.
 // After the producers' own barrier one thread writes off[L+2] (the end of
 // V_{L+1}) and publishes it with a release store of ctrl->ready = L + 2
 // (PTP_LEVELS_DONE once a level comes out empty), which the window CTAs
 // acquire before they read those offsets and queue entries.  Producers
 // never wait for the window CTAs.
-template <bool IPERM>
 __device__ __noinline__ void bfs_producer(const DistArgs &a) {
     const int P = a.producers;
     const int n = a.n;
@@ -87,7 +86,7 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a) {
                         if (atomicCAS(a.level + ww[e], -1, L + 1) == -1) {
                             const int at = atomicAdd(&a.ctrl->tail, 1);
                             a.queue_w[at] = ww[e];
-                            if (IPERM) a.iperm[ww[e]] = at;
+                            a.iperm[ww[e]] = at;
                         }
                 }
             }
@@ -108,7 +107,7 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a) {
                 for (int q = 0; q < PTP_RING; ++q)
                     if (claimed >> q & 1u) {
                         a.queue_w[at] = w[q];
-                        if (IPERM) a.iperm[w[q]] = at;
+                        a.iperm[w[q]] = at;
                         ++at;
                     }
             }
@@ -147,16 +146,21 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a) {
 // rearrangement, Sec. 5.1); otherwise position p is vertex p of the
 // renumbered mesh.  LABELS: also carry a label per vertex (Voronoi regions).
 //
-// FUSED (with PERM): the last a.producers CTAs run the BFS (bfs_producer)
-// while the others iterate; before iteration k a window CTA waits until the
-// offsets it reads (up to off[k+2]) are published.  rho is unknown until the
-// BFS ends; until then every CTA has seen at least k+2 published levels, so
-// rho > k+1 and j_k = k, the same decision the known rho would give.
+// FUSED (ptp_distance_from_sources): the toplesets are built inside this
+// launch.  The last a.producers CTAs run the BFS (bfs_producer); the others
+// run the iteration on a topleset-ordered copy of the mesh that they write
+// themselves, V_{k+1} during iteration k (copy_level), from the original
+// mesh with the slots remapped through iperm.  Before iteration k a window
+// CTA waits until off[0 .. k+3] are published (V_{k+2}'s positions are then
+// known, which the copy of V_{k+1} needs).  rho is unknown until the BFS
+// ends; until then every window CTA has seen at least k+3 published levels,
+// so rho > k+2 and j_k = k, the same decision the known rho would give.
 template <bool PERM, bool LABELS, bool FUSED = false>
 __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(DistArgs a) {
+    static_assert(!(FUSED && (PERM || LABELS)), "the fused window runs in topleset order, without labels");
     if constexpr (FUSED) {
         if ((int)blockIdx.x >= (int)gridDim.x - a.producers) {
-            bfs_producer<!PERM>(a);
+            bfs_producer(a);
             return;
         }
     }
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
 
     auto off_at = [&](int r) { return __ldcg(a.off + (r < rho ? r : rho)); };
     // the queue is written during a fused launch: read it through L2 there
-    auto vertex_at = [&](int pos) { return PERM ? (FUSED ? __ldcg(a.perm + pos) : __ldg(a.perm + pos)) : pos; };
+    auto vertex_at = [&](int pos) { return PERM ? __ldg(a.perm + pos) : pos; };
     // FUSED: wait until off[0 .. need] are published (or the BFS has ended);
     // afterwards rho is set if known.  Called by every thread of the CTA.
     // Returns false when a wait timed out or another CTA aborted.
@@ -227,13 +231,13 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     // what iteration k needs from the producers: offsets up to off[k+2]; in
     // topleset order also the positions of V_{k+2}, since iteration k copies
     // V_{k+1} (whose slots point into V_{k+2}) for iteration k+1
-    auto need_for = [](long long kk) { return PERM ? (int)kk + 2 : (int)kk + 3; };
+    auto need_for = [](long long kk) { return (int)kk + 3; };
     // FUSED in topleset order: copy the vertices at positions [pb, pe) from
     // the original mesh (slots remapped through iperm), 32-position chunks
     // dealt to the warps from the last one down, so that in a narrow band
     // the copying warps are not the ones with band chunks
     auto copy_level = [&](int pb, int pe) {
-        if constexpr (FUSED && !PERM) {
+        if constexpr (FUSED) {
             const int n = a.n;
             const int cb = pb & ~31;
             const int rch = pe > cb ? (pe - cb + 31) >> 5 : 0;
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     };
     // barrier epochs: the topleset-ordered fused run has one more barrier,
     // after copying V_0 and V_1, so its iteration k uses epoch k + 1
-    constexpr long long EP0 = (FUSED && !PERM) ? 1 : 0;
+    constexpr long long EP0 = FUSED ? 1 : 0;
     if constexpr (FUSED) {
         if (!wait_levels(need_for(1))) {
             status = PTP_ERR_TIMEOUT;
@@ -353,7 +357,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         // every slot is written, and the loads need not wait for meta.
         // (read through L2 when producers write them during this launch)
         auto load_slots = [&](int u, int &meta, int4 &r0, int4 &r1, float4 &l0, float4 &l1, float4 *g) {
-            constexpr bool CO = FUSED && !PERM;
+            constexpr bool CO = FUSED;
             meta = CO ? __ldcg(a.meta + u) : __ldg(a.meta + u);
             r0 = CO ? __ldcg(a.ring + u) : __ldg(a.ring + u);
             r1 = CO ? __ldcg(a.ring + a.n + u) : __ldg(a.ring + a.n + u);
@@ -462,7 +466,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             }
         }
         // V_{k+1} into topleset order for the next iteration
-        if constexpr (FUSED && !PERM) copy_level(off_at((int)k + 1), off_at((int)k + 2));
+        if constexpr (FUSED) copy_level(off_at((int)k + 1), off_at((int)k + 2));
         tot_active += n_active;
         tot_changed += n_changed;
 
@@ -685,11 +689,10 @@ ptp_status ptp_internal_window_occupancy(int block, int *per_sm) {
 namespace {
 
 // V_0 of a fused launch: off[0..1], the BFS state the producers start from,
-// and (renumbering) the sources' positions.
+// and the sources' positions.
 __global__ void fused_setup(ptp_ctrl *ctrl, int *off, const int *info, const int *queue, int *iperm) {
     const int m0 = info[3];  // unique sources, queued by the seeding kernel
-    if (iperm)
-        for (int q = threadIdx.x; q < m0; q += blockDim.x) iperm[queue[q]] = q;
+    for (int q = threadIdx.x; q < m0; q += blockDim.x) iperm[queue[q]] = q;
     if (threadIdx.x != 0) return;
     off[0] = 0;
     off[1] = m0;
@@ -712,14 +715,11 @@ __global__ void fused_gather(const ptp_ctrl *__restrict__ ctrl, int n, const int
 // vertices at a million), and one producer thread per frontier vertex keeps
 // a level to one round: 2 sqrt(n) threads, between 4096 and 8192, at most a
 // quarter of the grid (0 when the grid cannot split).
-ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, bool renum, bool labels, const void **fn,
-                       int *block, int *grid, int *producers) {
-    *fn = renum ? (const void *)ptp_window<false, false, true>
-                : labels ? (const void *)ptp_window<true, true, true> : (const void *)ptp_window<true, false, true>;
+ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int *block, int *grid, int *producers) {
     *block = window_block(params->block);
     if (*block < 0) return PTP_ERR_ARG;
     int per_sm = 0;
-    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, *fn, *block, 0));
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false, true>, *block, 0));
     if (per_sm < 1) return PTP_ERR_CUDA;
     *grid = per_sm * ptp_num_sms(mesh->device);
     if (params->grid > 0 && params->grid < *grid) *grid = params->grid;
@@ -733,10 +733,9 @@ ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, bool renu
 
 }  // namespace
 
-int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params, bool renum) {
-    const void *fn;
+int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params) {
     int block, grid, producers;
-    if (fused_shape(mesh, params, renum, false, &fn, &block, &grid, &producers) != PTP_OK) return 0;
+    if (fused_shape(mesh, params, &block, &grid, &producers) != PTP_OK) return 0;
     return producers;
 }
 
@@ -750,43 +749,27 @@ ptp_status ptp_internal_fused_gather(const ptp_mesh *mesh, const ptp_multi_bufs 
 }
 
 ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params, const int *src,
-                              const int *m_dev, int m_max, bool labels, const ptp_renum_bufs *rb, cudaStream_t s) {
+                              const int *m_dev, int m_max, const ptp_renum_bufs *rb, cudaStream_t s) {
     const int n = b->n;
     const int dev = mesh->device;
-    if (rb && labels) return PTP_ERR_ARG;
-    const void *fn;
     int block, grid, producers;
-    PTP_CHECK(fused_shape(mesh, params, rb != nullptr, labels, &fn, &block, &grid, &producers));
-    if (producers < 1) {
-        // too few CTAs to split: the BFS first, then the window in the
-        // original order (the distances then follow the original numbering)
-        if (rb) return PTP_ERR_TOO_LARGE;
-        PTP_CHECK(ptp_internal_bfs(mesh, b, src, m_dev, m_max, s));
-        return ptp_internal_window_multi(mesh, b, params, src, m_dev, m_max, labels, s);
-    }
+    PTP_CHECK(fused_shape(mesh, params, &block, &grid, &producers));
+    if (producers < 1) return PTP_ERR_TOO_LARGE;  // callers check ptp_internal_fused_producers first
     PTP_CHECK(ptp_internal_bfs_seed(mesh, b, src, m_dev, m_max, s));
     PTP_TRY(cudaMemsetAsync(b->ctrl, 0, sizeof(ptp_ctrl), s));
-    fused_setup<<<1, 256, 0, s>>>(b->ctrl, b->off, b->info, b->queue, rb ? rb->iperm : nullptr);
-    if (rb) {
-        // distances by position: the sources are positions [0, off[1])
-        init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(b->off, n, b->d0, b->d1, b->nstamp, b->chg);
-        ptp_count_launches(2);
-    } else {
-        init_multi<<<blocks_for(n, 256, dev), 256, 0, s>>>(n, b->d0, b->d1, b->nstamp, b->chg,
-                                                            labels ? b->lab0 : nullptr, labels ? b->lab1 : nullptr);
-        seed_multi<<<blocks_for(m_max, 256, dev), 256, 0, s>>>(src, m_max, m_dev, b->d0, b->d1,
-                                                               labels ? b->lab0 : nullptr, labels ? b->lab1 : nullptr);
-        ptp_count_launches(3);
-    }
+    fused_setup<<<1, 256, 0, s>>>(b->ctrl, b->off, b->info, b->queue, rb->iperm);
+    // distances by position: the sources are positions [0, off[1])
+    init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(b->off, n, b->d0, b->d1, b->nstamp, b->chg);
+    ptp_count_launches(2);
     PTP_TRY(cudaGetLastError());
     DistArgs a = {};
     a.n = n;
-    a.pos = rb ? rb->pos : mesh->pos;
-    a.ring = rb ? rb->ring : mesh->ring;
-    a.tgeom = rb ? rb->tgeom : mesh->tgeom;
-    a.elen = rb ? rb->elen : mesh->elen;
-    a.meta = rb ? rb->meta : mesh->meta;
-    a.row = mesh->row;  // original corner lists (GENERAL vertices map through iperm with rb)
+    a.pos = rb->pos;
+    a.ring = rb->ring;
+    a.tgeom = rb->tgeom;
+    a.elen = rb->elen;
+    a.meta = rb->meta;
+    a.row = mesh->row;  // original corner lists: GENERAL vertices map through iperm
     a.pairs = mesh->pairs;
     a.off = b->off;
     a.info = b->info;
@@ -801,34 +784,31 @@ ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp
     a.eps_abs = params->eps_abs;
     a.max_iter = params->max_iter;
     a.perm = b->queue;
-    a.lab0 = labels ? b->lab0 : nullptr;
-    a.lab1 = labels ? b->lab1 : nullptr;
     a.band_mode = params->band_mode;
     a.sched = nullptr;  // a schedule needs the whole toplesets first
     a.producers = producers;
+    a.level = b->level;
+    a.queue_w = b->queue;
+    a.off_w = b->off;
+    a.info_w = b->info;
     a.opos = mesh->pos;
     a.oring = mesh->ring;
     a.ometa = mesh->meta;
     a.otgeom = mesh->tgeom;
     a.oelen = mesh->elen;
-    if (rb) {
-        a.pos_w = rb->pos;
-        a.ring_w = rb->ring;
-        a.meta_w = rb->meta;
-        a.tgeom_w = rb->tgeom;
-        a.elen_w = rb->elen;
-        a.iperm = rb->iperm;
-        a.coherent = 1;
-    }
-    a.level = b->level;
-    a.queue_w = b->queue;
-    a.off_w = b->off;
-    a.info_w = b->info;
+    a.pos_w = rb->pos;
+    a.ring_w = rb->ring;
+    a.meta_w = rb->meta;
+    a.tgeom_w = rb->tgeom;
+    a.elen_w = rb->elen;
+    a.iperm = rb->iperm;
+    a.coherent = 1;
     if (params->trace && params->trace_cap > 0)
         PTP_TRY(cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s));
     void *args[] = {(void *)&a};
     if (params->ev_begin) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_begin, s));
-    PTP_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, s));
+    PTP_TRY(cudaLaunchCooperativeKernel((const void *)ptp_window<false, false, true>, dim3(grid), dim3(block), args, 0,
+                                        s));
     ptp_count_launches(1);
     if (params->ev_end) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_end, s));
     return PTP_OK;

@@ -140,16 +140,14 @@ ptp_status ptp_internal_mesh_geometry(ptp_mesh *mesh, cudaStream_t s);
 // the window kernel over b->queue in the original order.
 ptp_status ptp_internal_window_multi(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params,
                                      const int *src, const int *m_dev, int m_max, bool labels, cudaStream_t s);
-// The same map with the BFS running inside the window launch: seeds the
-// sources, initialises the distances and launches the fused window kernel,
-// whose last CTAs build the toplesets level by level into b->queue / off
-// while the others run the iteration as soon as the levels it needs exist.
-// Falls back to ptp_internal_bfs + ptp_internal_window_multi (or, with rb,
-// to the same steps in topleset order) when the grid is too small to split.
-// With `rb`, the producers also copy each level into topleset order (rb) one
-// level behind the BFS, and the window runs on that copy (positions; the
-// distances in b then follow the positions, rb->iperm maps back); without
-// it the window walks the queue over the original order (labels allowed).
+// The same map with the BFS running inside the window launch
+// (ptp_window<false, false, true>): seeds the sources, initialises the
+// distances by position and launches; the last CTAs build the toplesets
+// level by level into b->queue / off / level and rb->iperm while the others
+// copy each level into topleset order (rb) and iterate on it.  The
+// distances in b follow the positions (ptp_internal_fused_gather maps them
+// back).  PTP_ERR_TOO_LARGE when the grid is too small to split: callers
+// check ptp_internal_fused_producers first.
 struct ptp_renum_bufs {
     float4 *pos;    // [n]
     int4 *ring;     // [2 n]
@@ -159,11 +157,10 @@ struct ptp_renum_bufs {
     int *iperm;     // [n] original vertex -> position
 };
 ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params, const int *src,
-                              const int *m_dev, int m_max, bool labels, const ptp_renum_bufs *rb, cudaStream_t s);
-// Producer CTAs a fused launch with these params would get (0: the grid is
-// too small to split, and ptp_internal_fused would run the two steps).
-int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params, bool renum);
-// d_out (original order) from a run with rb.
+                              const int *m_dev, int m_max, const ptp_renum_bufs *rb, cudaStream_t s);
+// BFS CTAs a fused launch with these params gets (0: the grid is too small).
+int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params);
+// d_out (original order) from a fused run.
 ptp_status ptp_internal_fused_gather(const ptp_mesh *mesh, const ptp_multi_bufs *b, const ptp_renum_bufs *rb,
                                      float *d_out, cudaStream_t s);
 // The final distance (and label) buffer of the last window run in b.

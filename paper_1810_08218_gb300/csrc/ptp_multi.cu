@@ -228,11 +228,11 @@ extern "C" ptp_status ptp_distance_from_sources(ptp_mesh *mesh, const int32_t *s
     PTP_CHECK(ma.alloc(n, false, sizeof(int) * (size_t)m, &src_v, s));
     int *src = (int *)src_v;
     PTP_TRY(cudaMemcpyAsync(src, h.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
-    if (ptp_internal_fused_producers(mesh, params, true) > 0) {
+    if (ptp_internal_fused_producers(mesh, params) > 0) {
         // topleset-ordered copy written during the launch (200 B per vertex)
         RenumAlloc ra;
         PTP_CHECK(ra.alloc(n, s));
-        PTP_CHECK(ptp_internal_fused(mesh, &ma.b, params, src, nullptr, m, false, &ra.rb, s));
+        PTP_CHECK(ptp_internal_fused(mesh, &ma.b, params, src, nullptr, m, &ra.rb, s));
         PTP_CHECK(ptp_internal_fused_gather(mesh, &ma.b, &ra.rb, d_out, s));
     } else {
         // too few CTAs to split the launch: BFS, then the window in the original order
