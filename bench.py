@@ -69,11 +69,20 @@ def _dist_env():
     return rank, world, local
 
 
+STEPS = {
+    "uneven_batch32": "32 x ptp_mesh_create, 32 x ptp_toplesets on 8 streams (BFS, renumbering), "
+                      "ptp_batch_create, ptp_distance_batch (all 32 windows in one launch)",
+    "bumpy_l8_fps": "ptp_mesh_create, ptp_fps (1,000 samples: per sample BFS, window, device argmax, "
+                    "one captured CUDA graph), ptp_voronoi (64 seeds)",
+}
+SINGLE_STEP = ("ptp_mesh_create + ptp_distance_from_sources (corner lists and slots; BFS toplesets, "
+               "renumbering and the window iteration in one launch: all hot-path stages)")
+
+
 def _config(workload: str, world: int) -> dict:
     return {"workload": WORKLOADS[workload], "l2": "flushed between steps (256 MiB write)",
             "parallelism": f"independent replicas x{world}" if world > 1 else "single GPU",
-            "step": "ptp_mesh_create + ptp_distance_from_sources (corner lists and slots; BFS toplesets, "
-                    "renumbering and the window iteration in one launch: all hot-path stages)"}
+            "step": STEPS.get(workload, SINGLE_STEP)}
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -475,9 +484,10 @@ def run_batch(args) -> None:
     seq_params = capi.ptp_params_default(eps=1e-3)
 
     def sequential():
-        for (v, f, q), o in zip(dev, outs):
-            tops = capi.ptp_toplesets(capi.ptp_mesh_create(v, f), q)
-            capi.ptp_distance(tops, seq_params, o, stats=False)
+        # the same maps one after another, each through the single-map
+        # benchmark path (mesh, then the fused launch)
+        for (v, f, _), src, o in zip(dev, srcs, outs):
+            capi.ptp_distance_from_sources(capi.ptp_mesh_create(v, f), src, seq_params, o, stats=False)
 
     for _ in range(args.warmup):
         batched()

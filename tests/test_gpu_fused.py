@@ -129,3 +129,23 @@ def test_fused_argument_errors(capi):
     p.schedule = sched.data_ptr()
     with pytest.raises(capi.PTPError):
         capi.ptp_distance_from_sources(mesh, S, p, d)
+
+
+def test_fused_device_sources_and_geodesic(capi):
+    """Device source lists (validated on the host after a copy) and
+    ptp_geodesic (mesh + fused launch) give the same map."""
+    V, F = meshes.icosphere(5)
+    S = np.array([11, 4000, 11], dtype=np.int32)
+    mesh = capi.ptp_mesh_create(torch.from_numpy(f32(V)).cuda(), torch.from_numpy(F).cuda())
+    d_host = torch.empty(V.shape[0], dtype=torch.float32, device="cuda")
+    d_dev = torch.empty_like(d_host)
+    capi.ptp_distance_from_sources(mesh, S, capi.ptp_params_default(), d_host)
+    capi.ptp_distance_from_sources(mesh, torch.from_numpy(S).cuda(), capi.ptp_params_default(), d_dev)
+    assert torch.equal(d_host, d_dev)
+    tops = capi.ptp_toplesets(mesh, S)
+    d_two = torch.empty_like(d_host)
+    capi.ptp_distance(tops, capi.ptp_params_default(), d_two)
+    assert torch.equal(d_host, d_two)
+    out = np.empty(V.shape[0], dtype=np.float32)
+    st = capi.ptp_geodesic(f32(V), F, S, capi.ptp_params_default(), out)
+    assert st["status"] == 0 and np.array_equal(out, d_host.cpu().numpy())
