@@ -312,6 +312,17 @@ ptp_status ptp_autotune(ptp_toplesets_t *tops, ptp_batch_t *batch, ptp_params *p
                         ptp_tune_result *result);
 
 /*
+ * Self-test of the device-side wait limit (an addition of this library).
+ * Every wait in the library's kernels (grid barriers, the fused launch's
+ * waits for toplesets) gives up after a limit, flags PTP_ERR_TIMEOUT and
+ * returns, leaving the context usable.  This launches two CTAs that wait at
+ * a barrier sized for three, so the wait can only end by its limit of
+ * `cycles` SM clock cycles (1000 .. 4e9; else PTP_ERR_ARG).  Blocks.
+ * Returns PTP_ERR_TIMEOUT when the limit worked.
+ */
+ptp_status ptp_selftest_wait_limit(int64_t cycles, void *stream);
+
+/*
  * Geodesic Voronoi regions (Sec. 5.3, Voronoi diagrams from farthest-point
  * samples): one multi-source PTP map from the m seeds (Sec. 6.1.5, multi-source
  * problem; as in the paper's multi-source runs the vertices are not

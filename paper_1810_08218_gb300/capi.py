@@ -103,6 +103,7 @@ def load(path: str | None = None):
             "ptp_distance_batch": (st, [P, P, P, P, P]),
             "ptp_batch_destroy": (st, [P]),
             "ptp_autotune": (st, [P, P, P, i32, P, P]),
+            "ptp_selftest_wait_limit": (st, [i64, P]),
             "ptp_voronoi": (st, [P, P, i32, ctypes.c_int, P, P, P, P, P]),
             "ptp_window_features": (st, [P, P, P]),
             "ptp_mlp_infer": (st, [P, P, i32, P, ctypes.c_float, i32, P, P]),
@@ -372,6 +373,12 @@ def ptp_autotune(target, params: Params, reps: int = 3, stream=None) -> dict:
     _check(load().ptp_autotune(tops, batch, ctypes.byref(params), reps, _stream_ptr(stream), ctypes.byref(r)),
            "ptp_autotune")
     return r.as_dict()
+
+
+def ptp_selftest_wait_limit(cycles: int, stream=None) -> int:
+    """Status of a launch whose only wait can end by its limit alone
+    (PTP_ERR_TIMEOUT when the limit works)."""
+    return int(load().ptp_selftest_wait_limit(int(cycles), _stream_ptr(stream)))
 
 
 def ptp_voronoi(mesh: Mesh, seeds, params: Params, d_out=None, label_out=None, stream=None, stats: bool = True,

@@ -224,10 +224,11 @@ __device__ __forceinline__ unsigned long long ptp_atom_add_release_u64(unsigned 
 // carries those previous high halves.  Returns the sum, or -1 when the wait
 // timed out here (PTP_ERR_TIMEOUT is written to *status) or another CTA
 // flagged an abort; the caller must then leave its loop.  epoch starts at 1.
-// `parts` is the number of CTAs that take part (0: the whole grid).
+// `parts` is the number of CTAs that take part (0: the whole grid);
+// `limit` the wait's limit in SM clock cycles.
 __device__ __forceinline__ long long ptp_grid_sync(unsigned long long *words, long long epoch, unsigned value,
                                                    int *abort_flag, int *status, unsigned long long *prev_hi,
-                                                   unsigned parts = 0) {
+                                                   unsigned parts = 0, long long limit = PTP_WAIT_CYCLES) {
     __shared__ long long result_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -245,7 +246,7 @@ __device__ __forceinline__ long long ptp_grid_sync(unsigned long long *words, lo
                 if ((unsigned)v >= target) break;
                 if ((++spins & 63u) == 0) {
                     if (*(volatile int *)abort_flag) { res = -1; break; }
-                    if (clock64() - t0 > PTP_WAIT_CYCLES) {
+                    if (clock64() - t0 > limit) {
                         atomicExch(status, (int)PTP_ERR_TIMEOUT);
                         atomicExch(abort_flag, 1);
                         res = -1;

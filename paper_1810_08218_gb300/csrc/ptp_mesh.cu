@@ -465,3 +465,37 @@ extern "C" ptp_status ptp_mesh_destroy(ptp_mesh *m) {
     free(m);
     return e == cudaSuccess ? PTP_OK : ptp_internal_cuda_status(e);
 }
+
+// ---------------------------------------------------------------------------
+// Self-test of the device-side wait limit: every CTA of a cooperative launch
+// arrives at a grid barrier that counts one CTA more than the grid has, so
+// it can never complete; the wait gives up after `cycles` SM clock cycles,
+// flags PTP_ERR_TIMEOUT and the kernel returns.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+__global__ void wait_selftest(ptp_ctrl *ctrl, long long cycles) {
+    unsigned long long prev_hi[2] = {0ull, 0ull};
+    ptp_grid_sync(ctrl->bar, 1, 0u, &ctrl->abort, &ctrl->status, prev_hi, gridDim.x + 1, cycles);
+}
+
+}  // namespace
+
+extern "C" ptp_status ptp_selftest_wait_limit(int64_t cycles, void *stream) {
+    if (cycles < 1000 || cycles > 4000000000LL) return PTP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    ptp_ctrl *ctrl = nullptr;
+    PTP_TRY(cudaMallocAsync((void **)&ctrl, sizeof(ptp_ctrl), s));
+    cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(ptp_ctrl), s);
+    long long c = cycles;
+    void *args[] = {(void *)&ctrl, (void *)&c};
+    if (e == cudaSuccess) e = cudaLaunchCooperativeKernel((const void *)wait_selftest, dim3(2), dim3(32), args, 0, s);
+    if (e == cudaSuccess) ptp_count_launches(1);
+    int status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(ctrl, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return ptp_internal_cuda_status(e);
+    return (ptp_status)status;
+}

@@ -79,3 +79,11 @@ def test_autotune_argument_errors_before_cuda(lib):
     assert lib.ptp_autotune(None, None, ctypes.byref(p), 3, None, None) == capi.PTP_ERR_ARG  # neither target
     assert lib.ptp_autotune(ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.byref(p), 3, None, None) == capi.PTP_ERR_ARG
     assert lib.ptp_autotune(ctypes.c_void_p(8), None, None, 3, None, None) == capi.PTP_ERR_ARG
+
+
+def test_selftest_argument_errors_before_cuda(lib):
+    from paper_1810_08218_gb300 import capi
+
+    lib.ptp_selftest_wait_limit.argtypes = [ctypes.c_int64, ctypes.c_void_p]
+    assert lib.ptp_selftest_wait_limit(10, None) == capi.PTP_ERR_ARG
+    assert lib.ptp_selftest_wait_limit(10**12, None) == capi.PTP_ERR_ARG

@@ -243,3 +243,14 @@ def test_invalid_inputs(capi):
     with pytest.raises(capi.PTPError) as e:
         capi.ptp_toplesets(mesh, np.array([], dtype=np.int32))
     assert e.value.status == capi.PTP_ERR_ARG
+
+
+def test_device_wait_limit_ends_an_unfinishable_wait(capi):
+    """A barrier that can never complete (sized for one CTA more than the
+    grid) ends by its ~10 ms limit with PTP_ERR_TIMEOUT, and the context
+    stays usable: a map right after is still correct."""
+    assert capi.ptp_selftest_wait_limit(20_000_000) == capi.PTP_ERR_TIMEOUT
+    V, F, S = meshes.flat65()
+    g = run_gpu(capi, V, F, S)
+    o = run_oracle(V, F, S)
+    assert_close(g["d"], o.d, meshes.bbox_diagonal(V))
