@@ -194,38 +194,47 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     // FUSED: wait until off[0 .. need] are published (or the BFS has ended);
     // afterwards rho is set if known.  Called by every thread of the CTA.
     // Returns false when a wait timed out or another CTA aborted.
-    __shared__ int s_wait[2];
-    int seen = 1;  // thread 0: levels seen published (off[0], off[1] are set before launch)
+    // Every thread keeps the progress its CTA has seen (`seen`, updated by
+    // all threads from the same shared value after the barrier below, so it
+    // is uniform), and when the BFS is already far enough ahead (the common
+    // case) the CTA passes no barrier here; ctrl->ready is polled, by thread
+    // 0, only when it is not.  rho becomes known at the first poll after the
+    // BFS has ended, in every CTA before it needs it (need > rho by then).
+    // Consecutive calls are separated by a CTA barrier (the grid barrier),
+    // which keeps s_wait from being rewritten before every thread read it.
+    __shared__ int s_wait[3];
+    int seen = 1;  // off[0], off[1] are set before launch
     auto wait_levels = [&](int need) -> bool {
+        if (seen >= need) return true;
         if (threadIdx.x == 0) {
             int ok = 1;
-            if (seen < need) {
-                const long long t0 = clock64();
-                unsigned spins = 0;
-                while (true) {
-                    seen = ptp_ld_acquire_s32(&a.ctrl->ready);
-                    if (seen >= need) break;
-                    if ((++spins & 63u) == 0) {
-                        if (*(volatile int *)&a.ctrl->abort) { ok = 0; break; }
-                        if (clock64() - t0 > PTP_WAIT_CYCLES) {
-                            atomicExch(&a.ctrl->status, (int)PTP_ERR_TIMEOUT);
-                            atomicExch(&a.ctrl->abort, 1);
-                            ok = 0;
-                            break;
-                        }
+            int now = seen;
+            const long long t0 = clock64();
+            unsigned spins = 0;
+            while (true) {
+                now = ptp_ld_acquire_s32(&a.ctrl->ready);
+                if (now >= need) break;
+                if ((++spins & 63u) == 0) {
+                    if (*(volatile int *)&a.ctrl->abort) { ok = 0; break; }
+                    if (clock64() - t0 > PTP_WAIT_CYCLES) {
+                        atomicExch(&a.ctrl->status, (int)PTP_ERR_TIMEOUT);
+                        atomicExch(&a.ctrl->abort, 1);
+                        ok = 0;
+                        break;
                     }
                 }
             }
             s_wait[0] = ok;
-            s_wait[1] = (ok && seen == PTP_LEVELS_DONE) ? __ldcg(a.info) : RHO_UNKNOWN;
+            s_wait[1] = (ok && now == PTP_LEVELS_DONE) ? __ldcg(a.info) : RHO_UNKNOWN;
+            s_wait[2] = now;
         }
         __syncthreads();
         const bool ok = s_wait[0] != 0;
+        seen = s_wait[2];
         if (s_wait[1] != RHO_UNKNOWN && rho == RHO_UNKNOWN) {
             rho = s_wait[1];
             if (a.max_iter <= 0) max_iter = 8LL * rho + 64;
         }
-        __syncthreads();
         return ok;
     };
     // what iteration k needs from the producers: offsets up to off[k+2]; in
@@ -506,8 +515,8 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         const int sched_next = (a.sched && i + 1 < rho) ? __ldcg(a.sched + i + 1) : 1;
 
         const int any = __syncthreads_or(notconv);
-        const long long failed =
-            ptp_grid_sync(a.ctrl->bar, k + EP0, any ? 1u : 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)ncta);
+        const long long failed = ptp_grid_sync(a.ctrl->bar, k + EP0, any ? 1u : 0u, &a.ctrl->abort, &a.ctrl->status,
+                                               prev_hi, (unsigned)ncta, PTP_WAIT_CYCLES, true);
         if (failed < 0) {
             status = PTP_ERR_TIMEOUT;
             break;

@@ -225,12 +225,15 @@ __device__ __forceinline__ unsigned long long ptp_atom_add_release_u64(unsigned 
 // timed out here (PTP_ERR_TIMEOUT is written to *status) or another CTA
 // flagged an abort; the caller must then leave its loop.  epoch starts at 1.
 // `parts` is the number of CTAs that take part (0: the whole grid);
-// `limit` the wait's limit in SM clock cycles.
+// `limit` the wait's limit in SM clock cycles; `synced`: the caller has just
+// passed a CTA barrier (e.g. __syncthreads_or) after its last writes, so the
+// one on entry is skipped.
 __device__ __forceinline__ long long ptp_grid_sync(unsigned long long *words, long long epoch, unsigned value,
                                                    int *abort_flag, int *status, unsigned long long *prev_hi,
-                                                   unsigned parts = 0, long long limit = PTP_WAIT_CYCLES) {
+                                                   unsigned parts = 0, long long limit = PTP_WAIT_CYCLES,
+                                                   bool synced = false) {
     __shared__ long long result_s;
-    __syncthreads();
+    if (!synced) __syncthreads();
     if (threadIdx.x == 0) {
         const int w = (int)(epoch & 1);
         unsigned long long *word = words + w;
