@@ -122,6 +122,14 @@ ptp_status ptp_params_default(ptp_params *p);
  * (all devices, all entry points).  Never blocks. */
 int64_t ptp_kernel_launches(void);
 
+/* Return to the driver the device memory the library keeps for reuse.
+ * Every buffer the library allocates comes from its own stream-ordered
+ * memory pool per device, which keeps freed memory mapped so that the next
+ * call does not map it again; this trims those pools to what is still in
+ * use (nothing, once every handle is destroyed and its stream has
+ * finished).  Never blocks on a stream; PTP_ERR_CUDA on a CUDA error. */
+ptp_status ptp_release_memory(void);
+
 /*
  * Build the device mesh (Sec. 3.1, T = (V, E, F); Sec. 4.3 stores it as a
  * compact half-edge structure, here as vertex -> incident-triangle lists).

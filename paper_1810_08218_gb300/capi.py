@@ -89,6 +89,7 @@ def load(path: str | None = None):
             "ptp_status_str": (ctypes.c_char_p, [st]),
             "ptp_params_default": (st, [P]),
             "ptp_kernel_launches": (i64, []),
+            "ptp_release_memory": (st, []),
             "ptp_mesh_create": (st, [P, i64, P, i64, ctypes.c_int, P, P]),
             "ptp_mesh_info": (st, [P, P, P, P]),
             "ptp_mesh_destroy": (st, [P]),
@@ -231,6 +232,11 @@ def ptp_params_default(**overrides) -> Params:
 
 def ptp_kernel_launches() -> int:
     return int(load().ptp_kernel_launches())
+
+
+def ptp_release_memory() -> None:
+    """Trim the library's device memory pools to what is still in use."""
+    _check(load().ptp_release_memory(), "ptp_release_memory")
 
 
 def ptp_mesh_create(xyz, faces, stream=None) -> Mesh:

@@ -455,7 +455,7 @@ extern "C" ptp_status ptp_batch_create(ptp_toplesets_t *const *tops, int32_t cou
                             sizeof(int2) * (C > 0 ? C : 1), sizeof(int) * O, sizeof(int) * N,
                             sizeof(int) * MAPINFO * count};
     cudaError_t e = cudaSuccess;
-    for (int q = 0; q < 10 && e == cudaSuccess; ++q) e = cudaMallocAsync(ptrs[q], sizes[q], s);
+    for (int q = 0; q < 10 && e == cudaSuccess; ++q) e = ptp_malloc_async(ptrs[q], sizes[q], s);
     int64_t base = 0, cbase = 0, ostart = 0;
     for (int b = 0; b < count && e == cudaSuccess; ++b) {
         const ptp_toplesets_t *t = tops[b];
@@ -510,7 +510,7 @@ extern "C" ptp_status ptp_distance_batch(ptp_batch_t *bt, const ptp_params *para
     const size_t tail_bytes = 64 + 16 * MAXB + 4 * MAXB + sizeof(float *) * MAXB;
     const size_t head_bytes = ((16 * (size_t)N) + 255) & ~(size_t)255;
     char *scr = nullptr;
-    PTP_TRY(cudaMallocAsync((void **)&scr, head_bytes + ctrl_bytes + tail_bytes, s));
+    PTP_TRY(ptp_malloc_async((void **)&scr, head_bytes + ctrl_bytes + tail_bytes, s));
     float *d0 = (float *)scr;
     float *d1 = d0 + N;
     int *nstamp = (int *)(d1 + N);

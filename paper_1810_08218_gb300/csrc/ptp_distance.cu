@@ -856,8 +856,8 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
 
     float *dbuf = nullptr;
     int *ibuf = nullptr;
-    PTP_TRY(cudaMallocAsync((void **)&dbuf, sizeof(float) * 2 * n, s));
-    cudaError_t ce = cudaMallocAsync((void **)&ibuf, sizeof(int) * 2 * n, s);
+    PTP_TRY(ptp_malloc_async((void **)&dbuf, sizeof(float) * 2 * n, s));
+    cudaError_t ce = ptp_malloc_async((void **)&ibuf, sizeof(int) * 2 * n, s);
     if (ce != cudaSuccess) {
         cudaFreeAsync(dbuf, s);
         return ptp_internal_cuda_status(ce);
@@ -940,7 +940,7 @@ extern "C" ptp_status ptp_geodesic(const float *xyz, int64_t n_verts, const int3
     PTP_CHECK(ptp_mesh_create(xyz, n_verts, faces, n_faces, ptr_kind, stream, &mesh));
     float *dev_out = d_out;
     if (ptr_kind == PTP_HOST) {
-        cudaError_t ce = cudaMallocAsync((void **)&dev_out, sizeof(float) * n_verts, s);
+        cudaError_t ce = ptp_malloc_async((void **)&dev_out, sizeof(float) * n_verts, s);
         if (ce != cudaSuccess) {
             ptp_mesh_destroy(mesh);
             return ptp_internal_cuda_status(ce);

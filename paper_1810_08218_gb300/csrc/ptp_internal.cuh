@@ -168,6 +168,12 @@ __host__ __device__ inline int ptp_final_buffer(long long iterations) { return (
 
 int ptp_num_sms(int device);
 
+// Stream-ordered allocation from the library's own memory pool of the
+// current device (created on first use).  The pool keeps freed memory
+// mapped, so repeated calls do not map and unmap their buffers every time;
+// ptp_release_memory() returns it.  Freed with cudaFreeAsync.
+cudaError_t ptp_malloc_async(void **p, size_t bytes, cudaStream_t s);
+
 // Co-resident CTAs per SM of the single-map / batched window kernel
 // launched with `block` threads; 0 when it cannot launch.
 ptp_status ptp_internal_window_occupancy(int block, int *per_sm);

@@ -249,7 +249,7 @@ extern "C" ptp_status ptp_window_features(ptp_toplesets_t *t, float *feat_out, v
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)t->n;
     float *acc = nullptr;
-    PTP_TRY(cudaMallocAsync((void **)&acc, sizeof(float) * 8 * ((size_t)n + 1), s));
+    PTP_TRY(ptp_malloc_async((void **)&acc, sizeof(float) * 8 * ((size_t)n + 1), s));
     init_sums<<<blocks_for(8 * ((int64_t)n + 1), 256, t->device), 256, 0, s>>>(n, acc);
     window_sums<<<blocks_for(n, 256, t->device), 256, 0, s>>>(n, t->off, t->info, t->pos, t->meta, t->tgeom, t->elen,
                                                               acc);

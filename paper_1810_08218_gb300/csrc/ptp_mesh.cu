@@ -8,6 +8,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "ptp_internal.cuh"
 
 ptp_status ptp_internal_cuda_status(cudaError_t e) {
@@ -57,6 +59,54 @@ int ptp_num_sms(int device) {
     int v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
     return v > 0 ? v : 1;
+}
+
+namespace {
+
+constexpr int POOL_DEVICES = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[POOL_DEVICES] = {};
+
+}  // namespace
+
+cudaError_t ptp_malloc_async(void **p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= POOL_DEVICES) return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pools[dev]) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t np = nullptr;
+            e = cudaMemPoolCreate(&np, &props);
+            if (e != cudaSuccess) return e;
+            unsigned long long keep = ~0ull;  // keep freed memory until ptp_release_memory
+            e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(np);
+                return e;
+            }
+            g_pools[dev] = np;
+        }
+        pool = g_pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+extern "C" ptp_status ptp_release_memory(void) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (int d = 0; d < POOL_DEVICES; ++d) {
+        if (!g_pools[d]) continue;
+        const cudaError_t e = cudaMemPoolTrimTo(g_pools[d], 0);
+        if (e != cudaSuccess) return ptp_internal_cuda_status(e);
+    }
+    return PTP_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -371,17 +421,17 @@ extern "C" ptp_status ptp_mesh_create(const float *xyz, int64_t n_verts, const i
         }                                                \
     } while (0)
 
-    MESH_TRY(cudaMallocAsync((void **)&m->pos, sizeof(float4) * n_verts, s));
-    MESH_TRY(cudaMallocAsync((void **)&m->row, sizeof(int) * (n_verts + 1), s));
-    MESH_TRY(cudaMallocAsync((void **)&m->pairs, sizeof(int2) * nc, s));
-    MESH_TRY(cudaMallocAsync((void **)&m->ring, sizeof(int4) * 2 * n_verts, s));
-    MESH_TRY(cudaMallocAsync((void **)&m->meta, sizeof(int) * n_verts, s));
-    MESH_TRY(cudaMallocAsync((void **)&deg, sizeof(int) * (2 * n_verts + 8), s));
-    MESH_TRY(cudaMallocAsync((void **)&tmp, sizeof(int) * ptp_scan_tmp_ints(n_verts), s));
+    MESH_TRY(ptp_malloc_async((void **)&m->pos, sizeof(float4) * n_verts, s));
+    MESH_TRY(ptp_malloc_async((void **)&m->row, sizeof(int) * (n_verts + 1), s));
+    MESH_TRY(ptp_malloc_async((void **)&m->pairs, sizeof(int2) * nc, s));
+    MESH_TRY(ptp_malloc_async((void **)&m->ring, sizeof(int4) * 2 * n_verts, s));
+    MESH_TRY(ptp_malloc_async((void **)&m->meta, sizeof(int) * n_verts, s));
+    MESH_TRY(ptp_malloc_async((void **)&deg, sizeof(int) * (2 * n_verts + 8), s));
+    MESH_TRY(ptp_malloc_async((void **)&tmp, sizeof(int) * ptp_scan_tmp_ints(n_verts), s));
     err = deg + 2 * n_verts;  // [0] face errors, [2..7] bbox keys
     if (ptr_kind == PTP_HOST) {
-        MESH_TRY(cudaMallocAsync((void **)&xyz_d, sizeof(float) * 3 * n_verts, s));
-        MESH_TRY(cudaMallocAsync((void **)&F_d, sizeof(int) * nc, s));
+        MESH_TRY(ptp_malloc_async((void **)&xyz_d, sizeof(float) * 3 * n_verts, s));
+        MESH_TRY(ptp_malloc_async((void **)&F_d, sizeof(int) * nc, s));
         MESH_TRY(cudaMemcpyAsync(xyz_d, xyz, sizeof(float) * 3 * n_verts, cudaMemcpyHostToDevice, s));
         MESH_TRY(cudaMemcpyAsync(F_d, faces, sizeof(int) * nc, cudaMemcpyHostToDevice, s));
     } else {
@@ -486,7 +536,7 @@ extern "C" ptp_status ptp_selftest_wait_limit(int64_t cycles, void *stream) {
     if (cycles < 1000 || cycles > 4000000000LL) return PTP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     ptp_ctrl *ctrl = nullptr;
-    PTP_TRY(cudaMallocAsync((void **)&ctrl, sizeof(ptp_ctrl), s));
+    PTP_TRY(ptp_malloc_async((void **)&ctrl, sizeof(ptp_ctrl), s));
     cudaError_t e = cudaMemsetAsync(ctrl, 0, sizeof(ptp_ctrl), s);
     long long c = cycles;
     void *args[] = {(void *)&ctrl, (void *)&c};

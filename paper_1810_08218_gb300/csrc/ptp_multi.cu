@@ -118,7 +118,7 @@ struct MultiAlloc {
                                 4 * N,            4 * N,         labels ? 4 * N : 0, labels ? 4 * N : 0};
         size_t bytes = 0;
         for (size_t z : sizes) bytes += (z + 255) & ~(size_t)255;
-        PTP_TRY(cudaMallocAsync(&base, bytes + 256, st));
+        PTP_TRY(ptp_malloc_async(&base, bytes + 256, st));
         char *p = (char *)base;
         int q = 0;
         auto take = [&]() {
@@ -162,7 +162,7 @@ struct RenumAlloc {
                                 sizeof(float4) * PTP_TRI * N, sizeof(float4) * 2 * N, sizeof(int) * N};
         size_t bytes = 0;
         for (size_t z : parts) bytes += (z + 255) & ~(size_t)255;
-        PTP_TRY(cudaMallocAsync(&base, bytes, st));
+        PTP_TRY(ptp_malloc_async(&base, bytes, st));
         char *q = (char *)base;
         int i = 0;
         auto take = [&]() {

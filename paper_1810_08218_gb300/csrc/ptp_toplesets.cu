@@ -355,8 +355,8 @@ ptp_status ptp_internal_mesh_geometry(ptp_mesh *mesh, cudaStream_t s) {
     if (mesh->tgeom) return PTP_OK;
     const int64_t n = mesh->n;
     float4 *tg = nullptr, *el = nullptr;
-    PTP_TRY(cudaMallocAsync((void **)&tg, sizeof(float4) * PTP_TRI * n, s));
-    cudaError_t e = cudaMallocAsync((void **)&el, sizeof(float4) * 2 * n, s);
+    PTP_TRY(ptp_malloc_async((void **)&tg, sizeof(float4) * PTP_TRI * n, s));
+    cudaError_t e = ptp_malloc_async((void **)&el, sizeof(float4) * 2 * n, s);
     if (e != cudaSuccess) {
         cudaFreeAsync(tg, s);
         return ptp_internal_cuda_status(e);
@@ -414,27 +414,27 @@ extern "C" ptp_status ptp_toplesets(ptp_mesh *mesh, const int32_t *sources, int3
         }                                                \
     } while (0)
     {
-        TOPS_TRY(cudaMallocAsync((void **)&t->level, sizeof(int) * n, s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->perm, sizeof(int) * n, s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->iperm, sizeof(int) * n, s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->off, sizeof(int) * (n + 2), s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->info, sizeof(int) * 4, s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->pos, sizeof(float4) * n, s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->row, sizeof(int) * (n + 1), s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->ring, sizeof(int4) * 2 * n, s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->meta, sizeof(int) * n, s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->tgeom, sizeof(float4) * PTP_TRI * n, s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->elen, sizeof(float4) * 2 * n, s));
-        TOPS_TRY(cudaMallocAsync((void **)&t->ctrl, sizeof(ptp_ctrl), s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->level, sizeof(int) * n, s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->perm, sizeof(int) * n, s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->iperm, sizeof(int) * n, s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->off, sizeof(int) * (n + 2), s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->info, sizeof(int) * 4, s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->pos, sizeof(float4) * n, s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->row, sizeof(int) * (n + 1), s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->ring, sizeof(int4) * 2 * n, s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->meta, sizeof(int) * n, s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->tgeom, sizeof(float4) * PTP_TRI * n, s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->elen, sizeof(float4) * 2 * n, s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->ctrl, sizeof(ptp_ctrl), s));
         // work: counters [0..15], degrees [n], scan temp, BFS spill lists [2n]
         const int64_t scan_tmp = ptp_scan_tmp_ints(n);
-        TOPS_TRY(cudaMallocAsync((void **)&work, sizeof(int) * (16 + n + scan_tmp + 2 * n), s));
+        TOPS_TRY(ptp_malloc_async((void **)&work, sizeof(int) * (16 + n + scan_tmp + 2 * n), s));
         int *cnt = work;  // [0..2] spill counters, [4] unreached counter
         int *ndeg = work + 16;
         int *tmp = ndeg + n;
         int *spill = tmp + scan_tmp;
 
-        TOPS_TRY(cudaMallocAsync((void **)&src_d, sizeof(int) * m, s));
+        TOPS_TRY(ptp_malloc_async((void **)&src_d, sizeof(int) * m, s));
         TOPS_TRY(cudaMemcpyAsync(src_d, hsrc.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
         TOPS_TRY(cudaMemsetAsync(t->level, 0xFF, sizeof(int) * n, s));
         TOPS_TRY(cudaMemsetAsync(t->info, 0, sizeof(int) * 4, s));
@@ -462,7 +462,7 @@ extern "C" ptp_status ptp_toplesets(ptp_mesh *mesh, const int32_t *sources, int3
         st = ptp_exclusive_scan(ndeg, t->row, n, tmp, s);
         if (st != PTP_OK) goto fail;
         // corner lists, filled only for the vertices without a ring slot
-        TOPS_TRY(cudaMallocAsync((void **)&t->pairs, sizeof(int2) * t->ncorner, s));
+        TOPS_TRY(ptp_malloc_async((void **)&t->pairs, sizeof(int2) * t->ncorner, s));
         renumber_corners<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, t->iperm, (int)n, mesh->row, mesh->pairs,
                                                                 t->row, t->pairs);
         build_geometry<<<blocks_for(n, 128, dev), 128, 0, s>>>((int)n, t->pos, t->ring, t->meta, t->tgeom, t->elen);

@@ -63,7 +63,7 @@ extern "C" ptp_status ptp_autotune(ptp_toplesets_t *tops, ptp_batch_t *batch, pt
     int64_t total = 0;
     for (int b = 0; b < count; ++b) total += sizes[b];
     float *scratch = nullptr;
-    PTP_TRY(cudaMallocAsync((void **)&scratch, sizeof(float) * (total > 0 ? total : 1), s));
+    PTP_TRY(ptp_malloc_async((void **)&scratch, sizeof(float) * (total > 0 ? total : 1), s));
     float *outs[PTP_BATCH_MAX];
     {
         int64_t o = 0;

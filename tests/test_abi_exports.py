@@ -51,6 +51,8 @@ def test_host_only_entry_points(lib):
     out = ctypes.c_void_p()
     assert lib.ptp_mesh_create(None, 10, None, 1, 0, None, ctypes.byref(out)) == capi.PTP_ERR_ARG
     assert lib.ptp_params_default(None) == capi.PTP_ERR_ARG
+    # no pool has been created in a process without CUDA work: nothing to trim
+    assert lib.ptp_release_memory() == 0
 
 
 def test_batch_argument_errors_before_cuda(lib):

@@ -149,3 +149,20 @@ def test_fused_device_sources_and_geodesic(capi):
     out = np.empty(V.shape[0], dtype=np.float32)
     st = capi.ptp_geodesic(f32(V), F, S, capi.ptp_params_default(), out)
     assert st["status"] == 0 and np.array_equal(out, d_host.cpu().numpy())
+
+
+def test_pool_reuse_and_release(capi):
+    """Buffers reused from the library's pool, and buffers mapped again after
+    ptp_release_memory, give the same map."""
+    V, F = meshes.icosphere(5)
+    S = np.array([7], dtype=np.int32)
+    mesh = capi.ptp_mesh_create(torch.from_numpy(f32(V)).cuda(), torch.from_numpy(F).cuda())
+    outs = []
+    for r in range(3):
+        d = torch.empty(V.shape[0], dtype=torch.float32, device="cuda")
+        capi.ptp_distance_from_sources(mesh, S, capi.ptp_params_default(), d)
+        outs.append(d)
+        if r == 1:
+            torch.cuda.synchronize()
+            capi.ptp_release_memory()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
