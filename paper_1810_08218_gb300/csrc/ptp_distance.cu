@@ -32,18 +32,23 @@
 namespace {
 
 // BFS CTAs of the fused window launch: the toplesets (Sec. 4.1) level by
-// level into the queue.  Level L's entries queue[off[L], off[L+1]) are dealt
-// out one per producer thread and round (warps interleaved across the
-// producer CTAs); a lane loads its vertex's one-ring slot from the original
-// mesh and claims every neighbour still unvisited with atomicCAS (level -1 ->
-// L+1); a warp appends its claims to the queue with one atomicAdd on the
-// shared tail, recording each claimed vertex's position in iperm.
-// After the producers' own barrier one thread writes off[L+2] (the end of
-// V_{L+1}) and publishes it with a release store of ctrl->ready = L + 2
-// (PTP_LEVELS_DONE once a level comes out empty), which the window CTAs
-// acquire before they read those offsets and queue entries.  Producers
-// never wait for the window CTAs.
-__device__ __noinline__ void bfs_producer(const DistArgs &a) {
+// level into the queue.  Level L's entries (positions off[L] .. off[L+1])
+// are dealt out one per producer thread and round (warps interleaved across
+// the producer CTAs).  Every queued vertex has a record at its position in
+// the topleset-ordered meta and ring arrays (meta, and the one-ring slots
+// as original vertex ids, -1 past the count), written when it was claimed,
+// so a lane reads its entry's vertex, meta and slots in one coalesced round
+// trip and claims every unvisited ring neighbour with atomicCAS (level -1
+// -> L+1).  A warp stages its claims in shared memory; while one atomicAdd
+// on the shared tail reserves their positions, its lanes load the claims'
+// records from the original mesh, then write each claim's queue entry, iperm
+// and record.  The producers' own barrier sums what each CTA appended, so
+// after it one thread writes off[L+2] (the end of V_{L+1}) and publishes it
+// with a release store of ctrl->ready = L + 2 (PTP_LEVELS_DONE once a level
+// comes out empty), which the window CTAs acquire before they read those
+// offsets, queue entries and records; they remap the slots through iperm
+// when they copy the level.  Producers never wait for the window CTAs.
+__device__ __noinline__ void bfs_producer(const DistArgs &a, int *stage_smem) {
     const int P = a.producers;
     const int n = a.n;
     const int pid = (int)blockIdx.x - ((int)gridDim.x - P);
@@ -51,33 +56,45 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a) {
     const int pwarp = (int)(threadIdx.x >> 5) * P + pid;  // warps interleaved across the producer CTAs
     const int nthr = (int)blockDim.x * P;
     const int ptid = pwarp * 32 + lane;
+    int *const stage = stage_smem + (threadIdx.x >> 5) * (32 * PTP_RING);  // this warp's claims
+    __shared__ int s_app[2];  // vertices this CTA appended in level L: s_app[L & 1]
+    if (threadIdx.x == 0) s_app[0] = s_app[1] = 0;
+    __syncthreads();
     unsigned long long prev_hi[2] = {0ull, 0ull};
+    // queue entry, iperm and record of the vertex w claimed at position at
+    auto put = [&](int w, int at, int wm, int4 w0, int4 w1) {
+        const int vc = (wm & PTP_META_GENERAL) ? 0 : (wm & PTP_META_CNT);
+        a.queue_w[at] = w;
+        a.iperm[w] = at;
+        a.meta_w[at] = wm;
+        a.ring_w[at] = make_int4(vc > 0 ? w0.x : -1, vc > 1 ? w0.y : -1, vc > 2 ? w0.z : -1, vc > 3 ? w0.w : -1);
+        a.ring_w[n + at] = make_int4(vc > 4 ? w1.x : -1, vc > 5 ? w1.y : -1, vc > 6 ? w1.z : -1, vc > 7 ? w1.w : -1);
+    };
     int fbeg = 0;
-    int total = __ldcg(a.off + 1);  // V_0: the (unique) sources, already in the queue
+    int total = __ldcg(a.off + 1);  // V_0: the (unique) sources, queued with their records
     for (int L = 0;; ++L) {
+        int *const app = &s_app[L & 1];
         const int rounds = (total + nthr - 1) / nthr;
         for (int r = 0; r < rounds; ++r) {  // warp-uniform
             const int t = r * nthr + ptid;
-            const int u = t < total ? __ldcg(a.queue_w + fbeg + t) : -1;
-            const int m = u >= 0 ? __ldg(a.ometa + u) : PTP_META_GENERAL;
-            const int4 r0 = u >= 0 ? __ldg(a.oring + u) : make_int4(-1, -1, -1, -1);
-            const int4 r1 = u >= 0 ? __ldg(a.oring + n + u) : make_int4(-1, -1, -1, -1);
-            int w[PTP_RING];
+            const bool ok = t < total;
+            const int p = fbeg + t;
+            const int u = ok ? __ldcg(a.queue_w + p) : -1;
+            const int m = ok ? __ldcg(a.meta_w + p) : PTP_META_GENERAL;
+            const int4 r0 = ok ? __ldcg(a.ring_w + p) : make_int4(-1, -1, -1, -1);
+            const int4 r1 = ok ? __ldcg(a.ring_w + n + p) : make_int4(-1, -1, -1, -1);
+            const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
             unsigned claimed = 0;
             if (u >= 0 && !(m & PTP_META_GENERAL)) {
-                const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
                 const int cnt = m & PTP_META_CNT;
                 int old[PTP_RING];
 #pragma unroll
-                for (int q = 0; q < PTP_RING; ++q) {
-                    w[q] = ids[q];
-                    old[q] = q < cnt ? atomicCAS(a.level + ids[q], -1, L + 1) : 0;
-                }
+                for (int q = 0; q < PTP_RING; ++q) old[q] = q < cnt ? atomicCAS(a.level + ids[q], -1, L + 1) : 0;
 #pragma unroll
                 for (int q = 0; q < PTP_RING; ++q)
                     if (q < cnt && old[q] == -1) claimed |= 1u << q;
             } else if (u >= 0) {
-                // vertex without a ring slot: claim from its corner list
+                // vertex without a ring slot: claim from its corner lists
                 const int cb = __ldg(a.row + u), ce = __ldg(a.row + u + 1);
                 for (int c = cb; c < ce; ++c) {
                     const int2 pr = __ldg(a.pairs + c);
@@ -85,12 +102,13 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a) {
                     for (int e = 0; e < 2; ++e)
                         if (atomicCAS(a.level + ww[e], -1, L + 1) == -1) {
                             const int at = atomicAdd(&a.ctrl->tail, 1);
-                            a.queue_w[at] = ww[e];
-                            a.iperm[ww[e]] = at;
+                            put(ww[e], at, __ldg(a.ometa + ww[e]), __ldg(a.oring + ww[e]), __ldg(a.oring + n + ww[e]));
+                            atomicAdd(app, 1);
                         }
                 }
             }
-            // append the claimed ring neighbours, one atomic per warp
+            // the claimed ring neighbours: stage them, reserve their positions
+            // and load their records at once, then write them
             const int cntc = __popc(claimed);
             int incl = cntc;
 #pragma unroll
@@ -100,21 +118,39 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a) {
             }
             const int wtot = __shfl_sync(0xffffffffu, incl, 31);
             if (wtot) {
-                int at = 0;
-                if (lane == 31) at = atomicAdd(&a.ctrl->tail, wtot);
-                at = __shfl_sync(0xffffffffu, at, 31) + incl - cntc;
+                int idx = incl - cntc;
 #pragma unroll
                 for (int q = 0; q < PTP_RING; ++q)
-                    if (claimed >> q & 1u) {
-                        a.queue_w[at] = w[q];
-                        a.iperm[w[q]] = at;
-                        ++at;
-                    }
+                    if (claimed >> q & 1u) stage[idx++] = ids[q];
+                __syncwarp();
+                int at = 0;
+                if (lane == 31) {
+                    at = atomicAdd(&a.ctrl->tail, wtot);
+                    atomicAdd(app, wtot);
+                }
+                const int w0 = lane < wtot ? stage[lane] : -1;
+                const int w1 = lane + 32 < wtot ? stage[lane + 32] : -1;
+                const int4 none = make_int4(-1, -1, -1, -1);
+                const int m0 = w0 >= 0 ? __ldg(a.ometa + w0) : 0, m1 = w1 >= 0 ? __ldg(a.ometa + w1) : 0;
+                const int4 a0 = w0 >= 0 ? __ldg(a.oring + w0) : none, b0 = w0 >= 0 ? __ldg(a.oring + n + w0) : none;
+                const int4 a1 = w1 >= 0 ? __ldg(a.oring + w1) : none, b1 = w1 >= 0 ? __ldg(a.oring + n + w1) : none;
+                const int base = __shfl_sync(0xffffffffu, at, 31);
+                if (w0 >= 0) put(w0, base + lane, m0, a0, b0);
+                if (w1 >= 0) put(w1, base + lane + 32, m1, a1, b1);
+                for (int e = lane + 64; e < wtot; e += 32) {
+                    const int w = stage[e];
+                    put(w, base + e, __ldg(a.ometa + w), __ldg(a.oring + w), __ldg(a.oring + n + w));
+                }
+                __syncwarp();  // the stage is reused in the next round
             }
         }
-        if (ptp_grid_sync(a.ctrl->pbar, L + 1, 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)P) < 0) return;
-        const int end = __ldcg(&a.ctrl->tail);  // final: every append precedes the barrier
-        const int next = end - (fbeg + total);
+        __syncthreads();  // every append of this CTA is counted in *app
+        const unsigned val = (unsigned)*app;
+        if (threadIdx.x == 0) s_app[(L + 1) & 1] = 0;  // last read before the previous barrier
+        const long long next = ptp_grid_sync(a.ctrl->pbar, L + 1, val, &a.ctrl->abort, &a.ctrl->status, prev_hi,
+                                             (unsigned)P, PTP_WAIT_CYCLES, true);
+        if (next < 0) return;
+        const int end = fbeg + total + (int)next;
         if (pid == 0 && threadIdx.x == 0) {
             a.off_w[L + 2] = end;
             if (next == 0) {
@@ -127,7 +163,7 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a) {
         }
         if (next == 0) return;
         fbeg += total;
-        total = next;
+        total = (int)next;
     }
 }
 
@@ -148,9 +184,11 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a) {
 //
 // FUSED (ptp_distance_from_sources): the toplesets are built inside this
 // launch.  The last a.producers CTAs run the BFS (bfs_producer); the others
-// run the iteration on a topleset-ordered copy of the mesh that they write
-// themselves, V_{k+1} during iteration k (copy_level), from the original
-// mesh with the slots remapped through iperm.  Before iteration k a window
+// run the iteration on a topleset-ordered copy of the mesh: the producers
+// write each vertex's meta and raw slots at its position when they claim
+// it, and the window CTAs complete V_{k+1} during iteration k (copy_level)
+// with the slots remapped through iperm and the geometry copied from the
+// original mesh.  Before iteration k a window
 // CTA waits until off[0 .. k+3] are published (V_{k+2}'s positions are then
 // known, which the copy of V_{k+1} needs).  rho is unknown until the BFS
 // ends; until then every window CTA has seen at least k+3 published levels,
@@ -158,9 +196,12 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a) {
 template <bool PERM, bool LABELS, bool FUSED = false>
 __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(DistArgs a) {
     static_assert(!(FUSED && (PERM || LABELS)), "the fused window runs in topleset order, without labels");
+    __shared__ int2 s_queue[QUEUE_CAP];  // (vertex | in V_i << 31, bits of d_{k-1})
     if constexpr (FUSED) {
+        // the producers stage their claims in the window's queue, 256 ints a warp
+        static_assert(2 * QUEUE_CAP >= (DIST_THREADS / 32) * 32 * PTP_RING, "producer stage");
         if ((int)blockIdx.x >= (int)gridDim.x - a.producers) {
-            bfs_producer(a);
+            bfs_producer(a, reinterpret_cast<int *>(s_queue));
             return;
         }
     }
@@ -185,7 +226,6 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     __shared__ float s_max[DIST_THREADS / 32];
     __shared__ double s_sum[DIST_THREADS / 32];
     __shared__ int s_cnt[2][DIST_THREADS / 32];
-    __shared__ int2 s_queue[QUEUE_CAP];  // (vertex | in V_i << 31, bits of d_{k-1})
     __shared__ int s_nq;
 
     auto off_at = [&](int r) { return __ldcg(a.off + (r < rho ? r : rho)); };
@@ -241,10 +281,11 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     // topleset order also the positions of V_{k+2}, since iteration k copies
     // V_{k+1} (whose slots point into V_{k+2}) for iteration k+1
     auto need_for = [](long long kk) { return (int)kk + 3; };
-    // FUSED in topleset order: copy the vertices at positions [pb, pe) from
-    // the original mesh (slots remapped through iperm), 32-position chunks
-    // dealt to the warps from the last one down, so that in a narrow band
-    // the copying warps are not the ones with band chunks
+    // FUSED in topleset order: complete the vertices at positions [pb, pe)
+    // (their meta and raw slots are the producers' records): slots remapped
+    // through iperm, geometry copied from the original mesh.  32-position
+    // chunks are dealt to the warps from the last one down, so that in a
+    // narrow band the copying warps are not the ones with band chunks.
     auto copy_level = [&](int pb, int pe) {
         if constexpr (FUSED) {
             const int n = a.n;
@@ -254,17 +295,14 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                 const int p = cb + c * 32 + lane;
                 if (p < pb || p >= pe) continue;
                 const int v = __ldcg(a.perm + p);
-                const int vm = __ldg(a.ometa + v);
-                const int4 v0 = __ldg(a.oring + v), v1 = __ldg(a.oring + n + v);
+                const int4 s0 = __ldcg(a.ring_w + p), s1 = __ldcg(a.ring_w + n + p);
                 float4 g[PTP_TRI];
 #pragma unroll
                 for (int q = 0; q < PTP_TRI; ++q) g[q] = __ldg(a.otgeom + (size_t)q * n + v);
                 const float4 e0 = __ldg(a.oelen + v), e1 = __ldg(a.oelen + n + v), x = __ldg(a.opos + v);
-                const int vc = (vm & PTP_META_GENERAL) ? 0 : (vm & PTP_META_CNT);
-                auto mp = [&](int q, int id) { return q < vc ? __ldcg(a.iperm + id) : -1; };
-                a.ring_w[p] = make_int4(mp(0, v0.x), mp(1, v0.y), mp(2, v0.z), mp(3, v0.w));
-                a.ring_w[n + p] = make_int4(mp(4, v1.x), mp(5, v1.y), mp(6, v1.z), mp(7, v1.w));
-                a.meta_w[p] = vm;
+                auto mp = [&](int id) { return id >= 0 ? __ldcg(a.iperm + id) : -1; };
+                a.ring_w[p] = make_int4(mp(s0.x), mp(s0.y), mp(s0.z), mp(s0.w));
+                a.ring_w[n + p] = make_int4(mp(s1.x), mp(s1.y), mp(s1.z), mp(s1.w));
                 a.pos_w[p] = x;
 #pragma unroll
                 for (int q = 0; q < PTP_TRI; ++q) a.tgeom_w[(size_t)q * n + p] = g[q];
@@ -363,18 +401,18 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             }
         };
         // The geometry of every slot is loaded whatever the vertex's count:
-        // every slot is written, and the loads need not wait for meta.
-        // (read through L2 when producers write them during this launch)
+        // every slot is written, and the loads need not wait for meta.  The
+        // loads go through L2 only: a fused launch writes these arrays while
+        // it runs, and with the read-only cache the unfused kernel was no
+        // faster (a vertex is rarely recomputed on the same SM twice).
         auto load_slots = [&](int u, int &meta, int4 &r0, int4 &r1, float4 &l0, float4 &l1, float4 *g) {
-            constexpr bool CO = FUSED;
-            meta = CO ? __ldcg(a.meta + u) : __ldg(a.meta + u);
-            r0 = CO ? __ldcg(a.ring + u) : __ldg(a.ring + u);
-            r1 = CO ? __ldcg(a.ring + a.n + u) : __ldg(a.ring + a.n + u);
-            l0 = CO ? __ldcg(a.elen + u) : __ldg(a.elen + u);
-            l1 = CO ? __ldcg(a.elen + a.n + u) : __ldg(a.elen + a.n + u);
+            meta = __ldcg(a.meta + u);
+            r0 = __ldcg(a.ring + u);
+            r1 = __ldcg(a.ring + a.n + u);
+            l0 = __ldcg(a.elen + u);
+            l1 = __ldcg(a.elen + a.n + u);
 #pragma unroll
-            for (int t = 0; t < PTP_TRI; ++t)
-                g[t] = CO ? __ldcg(a.tgeom + (size_t)t * a.n + u) : __ldg(a.tgeom + (size_t)t * a.n + u);
+            for (int t = 0; t < PTP_TRI; ++t) g[t] = __ldcg(a.tgeom + (size_t)t * a.n + u);
         };
 
         if (nchunks <= nwarps) {
@@ -699,9 +737,20 @@ namespace {
 
 // V_0 of a fused launch: off[0..1], the BFS state the producers start from,
 // and the sources' positions.
-__global__ void fused_setup(ptp_ctrl *ctrl, int *off, const int *info, const int *queue, int *iperm) {
+__global__ void fused_setup(ptp_ctrl *ctrl, int *off, const int *info, const int *queue, int *iperm, int n,
+                            const int *__restrict__ ometa, const int4 *__restrict__ oring, int *meta_w, int4 *ring_w) {
     const int m0 = info[3];  // unique sources, queued by the seeding kernel
-    for (int q = threadIdx.x; q < m0; q += blockDim.x) iperm[queue[q]] = q;
+    for (int q = threadIdx.x; q < m0; q += blockDim.x) {
+        // position q, with the record the producers read (meta, raw slots)
+        const int v = queue[q];
+        iperm[v] = q;
+        const int vm = ometa[v];
+        const int vc = (vm & PTP_META_GENERAL) ? 0 : (vm & PTP_META_CNT);
+        const int4 w0 = oring[v], w1 = oring[n + v];
+        meta_w[q] = vm;
+        ring_w[q] = make_int4(vc > 0 ? w0.x : -1, vc > 1 ? w0.y : -1, vc > 2 ? w0.z : -1, vc > 3 ? w0.w : -1);
+        ring_w[n + q] = make_int4(vc > 4 ? w1.x : -1, vc > 5 ? w1.y : -1, vc > 6 ? w1.z : -1, vc > 7 ? w1.w : -1);
+    }
     if (threadIdx.x != 0) return;
     off[0] = 0;
     off[1] = m0;
@@ -766,7 +815,8 @@ ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp
     if (producers < 1) return PTP_ERR_TOO_LARGE;  // callers check ptp_internal_fused_producers first
     PTP_CHECK(ptp_internal_bfs_seed(mesh, b, src, m_dev, m_max, s));
     PTP_TRY(cudaMemsetAsync(b->ctrl, 0, sizeof(ptp_ctrl), s));
-    fused_setup<<<1, 256, 0, s>>>(b->ctrl, b->off, b->info, b->queue, rb->iperm);
+    fused_setup<<<1, 256, 0, s>>>(b->ctrl, b->off, b->info, b->queue, rb->iperm, n, mesh->meta, mesh->ring, rb->meta,
+                                  rb->ring);
     // distances by position: the sources are positions [0, off[1])
     init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(b->off, n, b->d0, b->d1, b->nstamp, b->chg);
     ptp_count_launches(2);
