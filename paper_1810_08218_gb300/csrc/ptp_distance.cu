@@ -770,9 +770,11 @@ __global__ void fused_gather(const ptp_ctrl *__restrict__ ctrl, int n, const int
 
 // Launch shape of a fused run: CTAs in all and how many run the BFS.  A
 // level's frontier grows like sqrt(n) on these meshes (a few thousand
-// vertices at a million), and one producer thread per frontier vertex keeps
-// a level to one round: 2 sqrt(n) threads, between 4096 and 8192, at most a
-// quarter of the grid (0 when the grid cannot split).
+// vertices at a million): 2 sqrt(n) producer threads, between 2048 and
+// 8192, at most a quarter of the grid (0 when the grid cannot split).  The
+// BFS paces the window only while the band is narrow, when the frontier is
+// still small, so the largest levels may take two rounds; every CTA spared
+// from the BFS runs the window, whose wide bands are throughput-bound.
 ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int *block, int *grid, int *producers) {
     *block = window_block(params->block);
     if (*block < 0) return PTP_ERR_ARG;
@@ -782,7 +784,7 @@ ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int *bloc
     *grid = per_sm * ptp_num_sms(mesh->device);
     if (params->grid > 0 && params->grid < *grid) *grid = params->grid;
     double th = 2.0 * sqrt((double)mesh->n);
-    th = th < 4096.0 ? 4096.0 : (th > 8192.0 ? 8192.0 : th);
+    th = th < 2048.0 ? 2048.0 : (th > 8192.0 ? 8192.0 : th);
     int p = ((int)th + *block - 1) / *block;
     if (p > *grid / 4) p = *grid / 4;
     *producers = p > 0 ? p : 0;
