@@ -509,10 +509,15 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                     load_slots(u, meta, r0, r1, l0, l1, g);
                     recompute(u, ent.x < 0, __int_as_float(ent.y), meta, r0, r1, l0, l1, g);
                 }
-                __syncthreads();
+                // the queue is refilled by the next round; after the last one
+                // only in the next iteration, behind the grid barrier, so warps
+                // done with pass 2 go on (to the level copy) at once
+                if (m0 + ROUND_CHUNKS < cta_m) __syncthreads();
             }
         }
-        // V_{k+1} into topleset order for the next iteration
+        // V_{k+1} into topleset order for the next iteration, by the warps
+        // counted from the last one down: in a narrow band not the band's
+        // warps, in a wide one the warps with the fewest queued vertices
         if constexpr (FUSED) copy_level(off_at((int)k + 1), off_at((int)k + 2));
         tot_active += n_active;
         tot_changed += n_changed;
