@@ -195,7 +195,7 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a, int *stage_smem) {
 // so rho > k+2 and j_k = k, the same decision the known rho would give.
 template <bool PERM, bool LABELS, bool FUSED = false>
 __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(DistArgs a) {
-    static_assert(!(FUSED && (PERM || LABELS)), "the fused window runs in topleset order, without labels");
+    static_assert(!(FUSED && LABELS && !PERM), "labels are carried in the original order");
     __shared__ int2 s_queue[QUEUE_CAP];  // (vertex | in V_i << 31, bits of d_{k-1})
     if constexpr (FUSED) {
         // the producers stage their claims in the window's queue, 256 ints a warp
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
 
     auto off_at = [&](int r) { return __ldcg(a.off + (r < rho ? r : rho)); };
     // the queue is written during a fused launch: read it through L2 there
-    auto vertex_at = [&](int pos) { return PERM ? __ldg(a.perm + pos) : pos; };
+    auto vertex_at = [&](int pos) { return PERM ? (FUSED ? __ldcg(a.perm + pos) : __ldg(a.perm + pos)) : pos; };
     // FUSED: wait until off[0 .. need] are published (or the BFS has ended);
     // afterwards rho is set if known.  Called by every thread of the CTA.
     // Returns false when a wait timed out or another CTA aborted.
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     };
     // barrier epochs: the topleset-ordered fused run has one more barrier,
     // after copying V_0 and V_1, so its iteration k uses epoch k + 1
-    constexpr long long EP0 = FUSED ? 1 : 0;
+    constexpr long long EP0 = (FUSED && !PERM) ? 1 : 0;
     if constexpr (FUSED) {
         if (!wait_levels(need_for(1))) {
             status = PTP_ERR_TIMEOUT;
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         // V_{k+1} into topleset order for the next iteration, by the warps
         // counted from the last one down: in a narrow band not the band's
         // warps, in a wide one the warps with the fewest queued vertices
-        if constexpr (FUSED) copy_level(off_at((int)k + 1), off_at((int)k + 2));
+        if constexpr (FUSED && !PERM) copy_level(off_at((int)k + 1), off_at((int)k + 2));
         tot_active += n_active;
         tot_changed += n_changed;
 
@@ -773,22 +773,31 @@ __global__ void fused_gather(const ptp_ctrl *__restrict__ ctrl, int n, const int
         d_out[v] = level[v] >= 0 ? d[iperm[v]] : INF;
 }
 
+// The fused window kernel: renumbered (topleset order, the single-map
+// path) or in the original order (multi-source maps, with or without labels).
+const void *fused_kernel(bool perm, bool labels) {
+    if (!perm) return (const void *)ptp_window<false, false, true>;
+    return labels ? (const void *)ptp_window<true, true, true> : (const void *)ptp_window<true, false, true>;
+}
+
 // Launch shape of a fused run: CTAs in all and how many run the BFS.  A
-// level's frontier grows like sqrt(n) on these meshes (a few thousand
-// vertices at a million): 2 sqrt(n) producer threads, between 2048 and
-// 8192, at most a quarter of the grid (0 when the grid cannot split).  The
-// BFS paces the window only while the band is narrow, when the frontier is
-// still small, so the largest levels may take two rounds; every CTA spared
-// from the BFS runs the window, whose wide bands are throughput-bound.
-ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int *block, int *grid, int *producers) {
+// level's frontier grows like sqrt(n) on these meshes from one source (a few
+// thousand vertices at a million), and like n / rho from many: 2 sqrt(n m)
+// producer threads for m sources, between 2048 and 8192, at most a quarter
+// of the grid (0 when the grid cannot split).  The BFS paces the window only
+// while the band is narrow, when the frontier is still small, so the largest
+// levels may take two rounds; every CTA spared from the BFS runs the window,
+// whose wide bands are throughput-bound.
+ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int m, bool perm, bool labels, int *block,
+                       int *grid, int *producers) {
     *block = window_block(params->block);
     if (*block < 0) return PTP_ERR_ARG;
     int per_sm = 0;
-    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false, true>, *block, 0));
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel(perm, labels), *block, 0));
     if (per_sm < 1) return PTP_ERR_CUDA;
     *grid = per_sm * ptp_num_sms(mesh->device);
     if (params->grid > 0 && params->grid < *grid) *grid = params->grid;
-    double th = 2.0 * sqrt((double)mesh->n);
+    double th = 2.0 * sqrt((double)mesh->n * (double)(m > 1 ? m : 1));
     th = th < 2048.0 ? 2048.0 : (th > 8192.0 ? 8192.0 : th);
     int p = ((int)th + *block - 1) / *block;
     if (p > *grid / 4) p = *grid / 4;
@@ -798,9 +807,9 @@ ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int *bloc
 
 }  // namespace
 
-int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params) {
+int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params, int m, bool perm, bool labels) {
     int block, grid, producers;
-    if (fused_shape(mesh, params, &block, &grid, &producers) != PTP_OK) return 0;
+    if (fused_shape(mesh, params, m, perm, labels, &block, &grid, &producers) != PTP_OK) return 0;
     return producers;
 }
 
@@ -814,28 +823,51 @@ ptp_status ptp_internal_fused_gather(const ptp_mesh *mesh, const ptp_multi_bufs 
 }
 
 ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params, const int *src,
-                              const int *m_dev, int m_max, const ptp_renum_bufs *rb, cudaStream_t s) {
+                              const int *m_dev, int m_max, bool perm, bool labels, const ptp_renum_bufs *rb,
+                              cudaStream_t s) {
     const int n = b->n;
     const int dev = mesh->device;
     int block, grid, producers;
-    PTP_CHECK(fused_shape(mesh, params, &block, &grid, &producers));
+    PTP_CHECK(fused_shape(mesh, params, m_max, perm, labels, &block, &grid, &producers));
     if (producers < 1) return PTP_ERR_TOO_LARGE;  // callers check ptp_internal_fused_producers first
     PTP_CHECK(ptp_internal_bfs_seed(mesh, b, src, m_dev, m_max, s));
     PTP_TRY(cudaMemsetAsync(b->ctrl, 0, sizeof(ptp_ctrl), s));
     fused_setup<<<1, 256, 0, s>>>(b->ctrl, b->off, b->info, b->queue, rb->iperm, n, mesh->meta, mesh->ring, rb->meta,
                                   rb->ring);
-    // distances by position: the sources are positions [0, off[1])
-    init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(b->off, n, b->d0, b->d1, b->nstamp, b->chg);
-    ptp_count_launches(2);
+    if (perm) {
+        // distances (and labels) in the original order
+        init_multi<<<blocks_for(n, 256, dev), 256, 0, s>>>(n, b->d0, b->d1, b->nstamp, b->chg,
+                                                            labels ? b->lab0 : nullptr, labels ? b->lab1 : nullptr);
+        seed_multi<<<blocks_for(m_max, 256, dev), 256, 0, s>>>(src, m_max, m_dev, b->d0, b->d1,
+                                                               labels ? b->lab0 : nullptr, labels ? b->lab1 : nullptr);
+        ptp_count_launches(3);
+    } else {
+        // distances by position: the sources are positions [0, off[1])
+        init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(b->off, n, b->d0, b->d1, b->nstamp, b->chg);
+        ptp_count_launches(2);
+    }
     PTP_TRY(cudaGetLastError());
     DistArgs a = {};
     a.n = n;
-    a.pos = rb->pos;
-    a.ring = rb->ring;
-    a.tgeom = rb->tgeom;
-    a.elen = rb->elen;
-    a.meta = rb->meta;
-    a.row = mesh->row;  // original corner lists: GENERAL vertices map through iperm
+    if (perm) {
+        // the window reads the original mesh; rb holds only the BFS's records
+        a.pos = mesh->pos;
+        a.ring = mesh->ring;
+        a.tgeom = mesh->tgeom;
+        a.elen = mesh->elen;
+        a.meta = mesh->meta;
+        a.lab0 = labels ? b->lab0 : nullptr;
+        a.lab1 = labels ? b->lab1 : nullptr;
+    } else {
+        a.pos = rb->pos;
+        a.ring = rb->ring;
+        a.tgeom = rb->tgeom;
+        a.elen = rb->elen;
+        a.meta = rb->meta;
+        a.gmap = rb->iperm;  // original corner lists: GENERAL vertices map through iperm
+        a.coherent = 1;
+    }
+    a.row = mesh->row;
     a.pairs = mesh->pairs;
     a.off = b->off;
     a.info = b->info;
@@ -868,13 +900,11 @@ ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp
     a.tgeom_w = rb->tgeom;
     a.elen_w = rb->elen;
     a.iperm = rb->iperm;
-    a.coherent = 1;
     if (params->trace && params->trace_cap > 0)
         PTP_TRY(cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s));
     void *args[] = {(void *)&a};
     if (params->ev_begin) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_begin, s));
-    PTP_TRY(cudaLaunchCooperativeKernel((const void *)ptp_window<false, false, true>, dim3(grid), dim3(block), args, 0,
-                                        s));
+    PTP_TRY(cudaLaunchCooperativeKernel(fused_kernel(perm, labels), dim3(grid), dim3(block), args, 0, s));
     ptp_count_launches(1);
     if (params->ev_end) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_end, s));
     return PTP_OK;

@@ -156,10 +156,14 @@ struct ptp_renum_bufs {
     float4 *elen;   // [2 n]
     int *iperm;     // [n] original vertex -> position
 };
+// perm: the window runs in the original order (multi-source maps; with
+// labels, Voronoi regions) and rb needs only meta, ring and iperm (the BFS
+// records); otherwise the renumbered single-map path (d by position).
 ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params, const int *src,
-                              const int *m_dev, int m_max, const ptp_renum_bufs *rb, cudaStream_t s);
-// BFS CTAs a fused launch with these params gets (0: the grid is too small).
-int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params);
+                              const int *m_dev, int m_max, bool perm, bool labels, const ptp_renum_bufs *rb,
+                              cudaStream_t s);
+// BFS CTAs a fused launch for m sources gets (0: the grid is too small).
+int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params, int m, bool perm, bool labels);
 // d_out (original order) from a fused run.
 ptp_status ptp_internal_fused_gather(const ptp_mesh *mesh, const ptp_multi_bufs *b, const ptp_renum_bufs *rb,
                                      float *d_out, cudaStream_t s);

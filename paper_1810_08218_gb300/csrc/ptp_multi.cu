@@ -155,11 +155,14 @@ struct RenumAlloc {
     ptp_renum_bufs rb;
     void *base = nullptr;
     cudaStream_t s = nullptr;
-    ptp_status alloc(int n, cudaStream_t st) {
+    // records_only: just what the BFS CTAs of an original-order run write
+    // (meta, slots, iperm)
+    ptp_status alloc(int n, cudaStream_t st, bool records_only = false) {
         s = st;
         const size_t N = (size_t)n;
-        const size_t parts[] = {sizeof(float4) * N, sizeof(int4) * 2 * N, sizeof(int) * N,
-                                sizeof(float4) * PTP_TRI * N, sizeof(float4) * 2 * N, sizeof(int) * N};
+        const size_t R = records_only ? 0 : N;
+        const size_t parts[] = {sizeof(float4) * R, sizeof(int4) * 2 * N, sizeof(int) * N,
+                                sizeof(float4) * PTP_TRI * R, sizeof(float4) * 2 * R, sizeof(int) * N};
         size_t bytes = 0;
         for (size_t z : parts) bytes += (z + 255) & ~(size_t)255;
         PTP_TRY(ptp_malloc_async(&base, bytes, st));
@@ -228,11 +231,11 @@ extern "C" ptp_status ptp_distance_from_sources(ptp_mesh *mesh, const int32_t *s
     PTP_CHECK(ma.alloc(n, false, sizeof(int) * (size_t)m, &src_v, s));
     int *src = (int *)src_v;
     PTP_TRY(cudaMemcpyAsync(src, h.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
-    if (ptp_internal_fused_producers(mesh, params) > 0) {
+    if (ptp_internal_fused_producers(mesh, params, m, false, false) > 0) {
         // topleset-ordered copy written during the launch (200 B per vertex)
         RenumAlloc ra;
         PTP_CHECK(ra.alloc(n, s));
-        PTP_CHECK(ptp_internal_fused(mesh, &ma.b, params, src, nullptr, m, &ra.rb, s));
+        PTP_CHECK(ptp_internal_fused(mesh, &ma.b, params, src, nullptr, m, false, false, &ra.rb, s));
         PTP_CHECK(ptp_internal_fused_gather(mesh, &ma.b, &ra.rb, d_out, s));
     } else {
         // too few CTAs to split the launch: BFS, then the window in the original order
@@ -277,8 +280,14 @@ extern "C" ptp_status ptp_voronoi(ptp_mesh *mesh, const int32_t *seeds, int32_t 
     PTP_CHECK(ma.alloc(n, true, sizeof(int) * (size_t)m, &src_v, s));
     int *src = (int *)src_v;
     PTP_TRY(cudaMemcpyAsync(src, h.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
-    PTP_CHECK(ptp_internal_bfs(mesh, &ma.b, src, nullptr, m, s));
-    PTP_CHECK(ptp_internal_window_multi(mesh, &ma.b, params, src, nullptr, m, true, s));
+    RenumAlloc ra;  // the BFS records of a fused run
+    if (ptp_internal_fused_producers(mesh, params, m, true, true) > 0) {
+        PTP_CHECK(ra.alloc(n, s, true));
+        PTP_CHECK(ptp_internal_fused(mesh, &ma.b, params, src, nullptr, m, true, true, &ra.rb, s));
+    } else {
+        PTP_CHECK(ptp_internal_bfs(mesh, &ma.b, src, nullptr, m, s));
+        PTP_CHECK(ptp_internal_window_multi(mesh, &ma.b, params, src, nullptr, m, true, s));
+    }
     multi_out<<<blocks_for(n, 256, mesh->device), 256, 0, s>>>(ma.b.ctrl, n, ma.b.d0, ma.b.d1, ma.b.lab0, ma.b.lab1,
                                                                 d_out, label_out);
     ptp_count_launches(1);
@@ -296,14 +305,19 @@ extern "C" ptp_status ptp_voronoi(ptp_mesh *mesh, const int32_t *seeds, int32_t 
 namespace {
 
 // One sampling step: map from samples[0 .. *m_dev), then append its argmax.
-// (A sampling map recomputes the whole mesh from the new source set, so its
-// cost is the window's wide iterations, not the BFS: the two steps in the
-// original order serve it as well as the fused launch.)
+// With rb (the BFS records) the map is one fused launch in the original
+// order (the toplesets built while the window runs, no copy into topleset
+// order: the paper also keeps multi-source maps in place, Sec. 5.1);
+// without, the BFS and the window run one after the other.
 ptp_status fps_step(ptp_mesh *mesh, ptp_multi_bufs *b, const ptp_params *params, int *samples, int *m_dev,
-                    int n_samples, FpsAccum *acc, cudaStream_t s) {
+                    int n_samples, FpsAccum *acc, const ptp_renum_bufs *rb, cudaStream_t s) {
     const int n = b->n;
-    PTP_CHECK(ptp_internal_bfs(mesh, b, samples, m_dev, n_samples, s));
-    PTP_CHECK(ptp_internal_window_multi(mesh, b, params, samples, m_dev, n_samples, false, s));
+    if (rb) {
+        PTP_CHECK(ptp_internal_fused(mesh, b, params, samples, m_dev, n_samples, true, false, rb, s));
+    } else {
+        PTP_CHECK(ptp_internal_bfs(mesh, b, samples, m_dev, n_samples, s));
+        PTP_CHECK(ptp_internal_window_multi(mesh, b, params, samples, m_dev, n_samples, false, s));
+    }
     argmax_key<<<blocks_for(n, 256, mesh->device), 256, 0, s>>>(b->ctrl, n, b->d0, b->d1, &acc->slot);
     fps_append<<<1, 32, 0, s>>>(acc, b->ctrl, b->info, samples, m_dev, n_samples);
     ptp_count_launches(2);
@@ -332,6 +346,10 @@ extern "C" ptp_status ptp_fps(ptp_mesh *mesh, int32_t first, int32_t n_samples, 
     FpsAccum *acc = (FpsAccum *)ex;
     int *m_dev = (int *)((char *)ex + ((sizeof(FpsAccum) + 255) & ~(size_t)255));
 
+    RenumAlloc ra;  // the BFS records of the fused sampling maps
+    const bool fused = ptp_internal_fused_producers(mesh, &p, n_samples, true, false) > 0;
+    if (fused) PTP_CHECK(ra.alloc(n, us, true));
+
     fps_init<<<1, 32, 0, us>>>(acc, samples_out, m_dev, first);
     ptp_count_launches(1);
     PTP_TRY(cudaGetLastError());
@@ -352,7 +370,7 @@ extern "C" ptp_status ptp_fps(ptp_mesh *mesh, int32_t first, int32_t n_samples, 
             int64_t per_step = 0;
             if (e == cudaSuccess) {
                 const int64_t c0 = ptp_kernel_launches();
-                st = fps_step(mesh, &ma.b, &p, samples_out, m_dev, n_samples, acc, cs);
+                st = fps_step(mesh, &ma.b, &p, samples_out, m_dev, n_samples, acc, fused ? &ra.rb : nullptr, cs);
                 per_step = ptp_kernel_launches() - c0;
                 const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
                 if (st == PTP_OK && e2 != cudaSuccess) e = e2;
@@ -375,7 +393,7 @@ extern "C" ptp_status ptp_fps(ptp_mesh *mesh, int32_t first, int32_t n_samples, 
             if (st == PTP_OK && e != cudaSuccess) st = ptp_internal_cuda_status(e);
         } else {
             for (int i = 1; st == PTP_OK && i < n_samples; ++i)
-                st = fps_step(mesh, &ma.b, &p, samples_out, m_dev, n_samples, acc, us);
+                st = fps_step(mesh, &ma.b, &p, samples_out, m_dev, n_samples, acc, fused ? &ra.rb : nullptr, us);
         }
     }
     if (st != PTP_OK) return st;

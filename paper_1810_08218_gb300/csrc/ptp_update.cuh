@@ -64,6 +64,7 @@ struct DistArgs {
     float4 *tgeom_w;
     float4 *elen_w;
     int *iperm;
+    const int *gmap;  // renumbered fused launch: original vertex -> position for the corner lists (= iperm)
     int coherent;     // the renumbered arrays are written during the launch: load them through L2
 };
 
@@ -209,15 +210,15 @@ __device__ __forceinline__ float update_ring(const DistArgs &a, int u, const int
 // New value of a GENERAL vertex from its corner list.
 __device__ __noinline__ float update_general(const DistArgs &a, int u, float best, const float *__restrict__ dp,
                                              const int *__restrict__ lp, int *label, unsigned &nfp64) {
-    // With a.iperm (fused, renumbered) the corner lists are the original ones:
+    // With a.gmap (fused, renumbered) the corner lists are the original ones:
     // vertex u is original vertex perm[u] and a corner's ids map through iperm.
-    const bool fmap = a.iperm != nullptr;
+    const bool fmap = a.gmap != nullptr;
     const int v = fmap ? __ldcg(a.perm + u) : u;
     const float3 x0 = xyz(fmap ? __ldg(a.opos + v) : __ldg(a.pos + u));
     const int cb = __ldg(a.row + v), ce = __ldg(a.row + v + 1);
     for (int c = cb; c < ce; ++c) {
         const int2 pr = __ldg(a.pairs + c);
-        const int p1 = fmap ? __ldcg(a.iperm + pr.x) : pr.x, p2 = fmap ? __ldcg(a.iperm + pr.y) : pr.y;
+        const int p1 = fmap ? __ldcg(a.gmap + pr.x) : pr.x, p2 = fmap ? __ldcg(a.gmap + pr.y) : pr.y;
         const float d1 = __ldcg(dp + p1), d2 = __ldcg(dp + p2);
         if (!(fminf(d1, d2) < best)) continue;
         const float3 x1 = xyz(fmap ? __ldg(a.opos + pr.x) : __ldg(a.pos + pr.x));
@@ -234,13 +235,13 @@ __device__ __noinline__ float update_general(const DistArgs &a, int u, float bes
 }
 
 __device__ __noinline__ void stamp_general(const DistArgs &a, int u, int k) {
-    const bool fmap = a.iperm != nullptr;
+    const bool fmap = a.gmap != nullptr;
     const int v = fmap ? __ldcg(a.perm + u) : u;
     const int cb = __ldg(a.row + v), ce = __ldg(a.row + v + 1);
     for (int c = cb; c < ce; ++c) {
         const int2 pr = __ldg(a.pairs + c);
-        a.nstamp[fmap ? __ldcg(a.iperm + pr.x) : pr.x] = k;
-        a.nstamp[fmap ? __ldcg(a.iperm + pr.y) : pr.y] = k;
+        a.nstamp[fmap ? __ldcg(a.gmap + pr.x) : pr.x] = k;
+        a.nstamp[fmap ? __ldcg(a.gmap + pr.y) : pr.y] = k;
     }
 }
 
