@@ -783,11 +783,13 @@ const void *fused_kernel(bool perm, bool labels) {
 // Launch shape of a fused run: CTAs in all and how many run the BFS.  A
 // level's frontier grows like sqrt(n) on these meshes from one source (a few
 // thousand vertices at a million), and like n / rho from many: 2 sqrt(n m)
-// producer threads for m sources, between 2048 and 8192, at most a quarter
-// of the grid (0 when the grid cannot split).  The BFS paces the window only
-// while the band is narrow, when the frontier is still small, so the largest
-// levels may take two rounds; every CTA spared from the BFS runs the window,
-// whose wide bands are throughput-bound.
+// producer threads for m sources, from 2048 up to 8192 for one source and
+// 16384 for several, at most a quarter of the grid (0 when the grid cannot
+// split).  From one source the BFS paces the window only while the band is
+// narrow, when the frontier is still small, so the largest levels may take
+// two rounds and every CTA spared from the BFS runs the window, whose wide
+// bands are throughput-bound; a multi-source map (K close to rho, wide
+// frontiers from the first level) is paced by the BFS throughout.
 ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int m, bool perm, bool labels, int *block,
                        int *grid, int *producers) {
     *block = window_block(params->block);
@@ -798,7 +800,8 @@ ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int m, bo
     *grid = per_sm * ptp_num_sms(mesh->device);
     if (params->grid > 0 && params->grid < *grid) *grid = params->grid;
     double th = 2.0 * sqrt((double)mesh->n * (double)(m > 1 ? m : 1));
-    th = th < 2048.0 ? 2048.0 : (th > 8192.0 ? 8192.0 : th);
+    const double th_max = m > 1 ? 16384.0 : 8192.0;
+    th = th < 2048.0 ? 2048.0 : (th > th_max ? th_max : th);
     int p = ((int)th + *block - 1) / *block;
     if (p > *grid / 4) p = *grid / 4;
     *producers = p > 0 ? p : 0;
