@@ -341,6 +341,8 @@ ptp_status ptp_selftest_wait_limit(int64_t cycles, void *stream);
  *             first index.
  *  d_out      [n_verts] float32 DEVICE, distance to the nearest seed.
  *  label_out  [n_verts] int32 DEVICE, seed index, -1 where unreachable.
+ *  The map is one launch that builds the toplesets while the window runs
+ *  (40 B per vertex of scratch besides the distances and labels).
  *  Blocks only when stats is non-NULL (as ptp_distance).
  */
 ptp_status ptp_voronoi(ptp_mesh *mesh, const int32_t *seeds, int32_t m, int ptr_kind, const ptp_params *params,
@@ -353,7 +355,8 @@ ptp_status ptp_voronoi(ptp_mesh *mesh, const int32_t *seeds, int32_t m, int ptr_
  * unreachable vertex counts as infinitely far).  Everything stays on the
  * device: the argmax, the sample list and the source count are device data,
  * and with use_graph != 0 one sampling step is captured once as a CUDA graph
- * and relaunched for every sample.
+ * and relaunched for every sample.  Each map is one launch that builds the
+ * toplesets while the window runs.
  *  samples_out  [n_samples] int32 DEVICE: first, then the chosen samples.
  *  d_out        [n_verts] float32 DEVICE or NULL: distance to all n_samples
  *               samples (one more map).
