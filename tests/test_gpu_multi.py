@@ -109,3 +109,29 @@ def test_fps_graph_and_stream_paths_agree(capi):
     sb = capi.ptp_fps(mesh, 3, 40, capi.ptp_params_default(), b, use_graph=True)
     assert torch.equal(a, b)
     assert sa["iterations"] == sb["iterations"] and sa["band_updates"] == sb["band_updates"]
+
+
+def test_fused_and_two_step_multi_source_agree(capi):
+    """Voronoi and FPS maps as one fused launch (the default) and, on a grid
+    too small to split (3 CTAs), as the BFS followed by the window: the same
+    iterates, so identical distances, labels and samples."""
+    V, F = meshes.bumpy_icosphere(5, 64, 0.05, 0.1, seed=6)
+    n = V.shape[0]
+    mesh = mesh_of(capi, V, F)
+    seeds = np.random.default_rng(7).choice(n, size=12, replace=False).astype(np.int32)
+    runs = []
+    for grid in (0, 3):
+        p = capi.ptp_params_default(grid=grid)
+        d = torch.empty(n, dtype=torch.float32, device="cuda")
+        lab = torch.empty(n, dtype=torch.int32, device="cuda")
+        sv = capi.ptp_voronoi(mesh, seeds, p, d, lab)
+        smp = torch.empty(20, dtype=torch.int32, device="cuda")
+        df = torch.empty(n, dtype=torch.float32, device="cuda")
+        sf = capi.ptp_fps(mesh, 11, 20, p, smp, df, use_graph=True)
+        assert sv["status"] == 0 and sf["status"] == 0
+        runs.append((d, lab, sv, smp, df, sf))
+    (d0, l0, v0, s0, f0, p0), (d1, l1, v1, s1, f1, p1) = runs
+    assert torch.equal(d0, d1) and torch.equal(l0, l1)
+    assert v0["iterations"] == v1["iterations"] and v0["band_updates"] == v1["band_updates"]
+    assert torch.equal(s0, s1) and torch.equal(f0, f1)
+    assert p0["iterations"] == p1["iterations"] and p0["band_updates"] == p1["band_updates"]
