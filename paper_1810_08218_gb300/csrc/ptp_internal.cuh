@@ -54,8 +54,9 @@ struct ptp_ctrl {
     // BFS running inside the window launch (ptp_distance_from_sources):
     unsigned long long pbar[2];  // barrier words of the BFS CTAs
     int tail;                    // BFS queue length so far
-    int ready;                   // levels published: off[0 .. ready] and their queue entries
-                                 // are final (PTP_LEVELS_DONE once the BFS has ended)
+    int ready;                   // levels published: off[0 .. ready] and the queue entries,
+                                 // records and iperm of V_0 .. V_{ready-1} are final
+                                 // (PTP_LEVELS_DONE once the BFS has ended)
 };
 
 #define PTP_LEVELS_DONE 0x7fffffff
