@@ -273,11 +273,28 @@ __global__ void pack_positions(const float *__restrict__ xyz, int64_t n, float4 
             mx[q] = fmaxf(mx[q], __shfl_xor_sync(0xffffffffu, mx[q], o));
         }
     }
+    // then across the CTA's warps, so that only one atomic per CTA and key
+    // reaches the six shared words
+    __shared__ float s_mn[3][32], s_mx[3][32];
+    const int wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     if ((threadIdx.x & 31) == 0) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            atomicMin(&bb[q], float_key(mn[q]));
-            atomicMax(&bb[3 + q], float_key(mx[q]));
+            s_mn[q][wid] = mn[q];
+            s_mx[q][wid] = mx[q];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float a = s_mn[q][0], b = s_mx[q][0];
+            for (int w = 1; w < nw; ++w) {
+                a = fminf(a, s_mn[q][w]);
+                b = fmaxf(b, s_mx[q][w]);
+            }
+            atomicMin(&bb[q], float_key(a));
+            atomicMax(&bb[3 + q], float_key(b));
         }
     }
 }
