@@ -261,14 +261,15 @@ __global__ void __launch_bounds__(DIST_THREADS, 1) ptp_window_batch(BatchArgs ba
                 const int b = (ent.x >> NBITS) & 31;
                 const bool in_vi = ent.x < 0;
                 const float dold = __int_as_float(ent.y);
-                const int meta = __ldg(a.meta + u);
-                const int4 r0 = __ldg(a.ring + u), r1 = __ldg(a.ring + a.n + u);
-                const float4 l0 = __ldg(a.elen + u), l1 = __ldg(a.elen + a.n + u);
+                // through L2 only, as in the single-map kernel
+                const int meta = __ldcg(a.meta + u);
+                const int4 r0 = __ldcg(a.ring + u), r1 = __ldcg(a.ring + a.n + u);
+                const float4 l0 = __ldcg(a.elen + u), l1 = __ldcg(a.elen + a.n + u);
                 const int mm = meta & PTP_META_CNT;
                 float4 g[PTP_TRI];
 #pragma unroll
                 for (int t = 0; t < PTP_TRI; ++t)
-                    g[t] = __ldg(a.tgeom + (size_t)t * a.n + u);  // every slot is written: no wait on meta
+                    g[t] = __ldcg(a.tgeom + (size_t)t * a.n + u);  // every slot is written: no wait on meta
                 const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
                 const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
                 int label = 0;
@@ -294,7 +295,9 @@ __global__ void __launch_bounds__(DIST_THREADS, 1) ptp_window_batch(BatchArgs ba
                     }
                 }
             }
-            __syncthreads();
+            // the next round refills the queue; after the last one the CTA
+            // barrier below comes first
+            if (m0 + ROUND_CHUNKS < cta_m) __syncthreads();
         }
         tot_active += n_active;
         tot_changed += n_changed;
