@@ -111,11 +111,16 @@ def test_fps_graph_and_stream_paths_agree(capi):
     assert sa["iterations"] == sb["iterations"] and sa["band_updates"] == sb["band_updates"]
 
 
-def test_fused_and_two_step_multi_source_agree(capi):
+@pytest.mark.parametrize("name", ["bumpy", "delaunay"])
+def test_fused_and_two_step_multi_source_agree(capi, name):
     """Voronoi and FPS maps as one fused launch (the default) and, on a grid
     too small to split (3 CTAs), as the BFS followed by the window: the same
-    iterates, so identical distances, labels and samples."""
-    V, F = meshes.bumpy_icosphere(5, 64, 0.05, 0.1, seed=6)
+    iterates, so identical distances, labels and samples.  The Delaunay mesh
+    has vertices updated from their corner lists (no ring slot)."""
+    if name == "bumpy":
+        V, F = meshes.bumpy_icosphere(5, 64, 0.05, 0.1, seed=6)
+    else:
+        V, F = meshes.random_planar(20000, seed=8)
     n = V.shape[0]
     mesh = mesh_of(capi, V, F)
     seeds = np.random.default_rng(7).choice(n, size=12, replace=False).astype(np.int32)
