@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -70,8 +71,9 @@ def _dist_env():
 
 
 STEPS = {
-    "uneven_batch32": "32 x ptp_mesh_create, 32 x ptp_toplesets on 8 streams (BFS, renumbering), "
-                      "ptp_batch_create, ptp_distance_batch (all 32 windows in one launch)",
+    "uneven_batch32": "32 x (ptp_mesh_create + ptp_toplesets) on 8 streams, largest mesh first to the least "
+                      "loaded stream (BFS, renumbering), ptp_batch_create, ptp_distance_batch (all 32 windows in "
+                      "one launch)",
     "bumpy_l8_fps": "ptp_mesh_create, ptp_fps (1,000 samples: per sample BFS, window, device argmax, "
                     "one captured CUDA graph), ptp_voronoi (64 seeds)",
 }
@@ -455,21 +457,32 @@ def run_batch(args) -> None:
     params.ev_begin = kb.cuda_event
     params.ev_end = ke.cuda_event
     res = {}
-    # The meshes' toplesets are independent: each BFS occupies one 8-SM
-    # cluster, so they are built on 8 streams at once (host source lists, so
-    # no call waits for the device) and joined before the batch is created.
+    # The meshes and their toplesets are independent: each BFS occupies one
+    # 8-SM cluster, so they are built on 8 streams at once (host source lists,
+    # so no toplesets call waits for the device) and joined before the batch
+    # is created.  A BFS takes time in proportion to its levels, about
+    # sqrt(n), so the meshes go largest first to the least loaded stream; a
+    # mesh is created on its own stream, so its validation read-back waits
+    # only for that stream while the others run.
     side = [torch.cuda.Stream() for _ in range(8)]
     srcs = [np.ascontiguousarray(S, dtype=np.int32) for _, _, S in probs]
+    order = sorted(range(len(sizes)), key=lambda i: -sizes[i])
+    load = [0.0] * len(side)
+    lane_of = {}
+    for i in order:
+        j = min(range(len(side)), key=lambda q: load[q])
+        lane_of[i] = j
+        load[j] += math.sqrt(sizes[i])
 
     def batched(src=dev, out_host=False):
-        meshes_ = [capi.ptp_mesh_create(v, f) for v, f, _ in src]
         ready = torch.cuda.Event()
         ready.record(stream)
-        tops = []
-        for i, m in enumerate(meshes_):
-            ss = side[i % len(side)]
+        for ss in side:
             ss.wait_event(ready)
-            tops.append(capi.ptp_toplesets(m, srcs[i], stream=ss))
+        tops = [None] * len(src)
+        for i in order:
+            ss = side[lane_of[i]]
+            tops[i] = capi.ptp_toplesets(capi.ptp_mesh_create(src[i][0], src[i][1], stream=ss), srcs[i], stream=ss)
         for ss in side:
             ev = torch.cuda.Event()
             ev.record(ss)
