@@ -427,6 +427,19 @@ def _timed_steps(torch, stream, flush, step, n):
     return out
 
 
+def stream_schedule(sizes, lanes):
+    """Largest first to the least loaded lane, the load of a mesh being
+    sqrt(n) (its BFS levels).  Returns the issue order and lane per mesh."""
+    order = sorted(range(len(sizes)), key=lambda i: (-sizes[i], i))
+    load = [0.0] * lanes
+    lane_of = {}
+    for i in order:
+        j = min(range(lanes), key=lambda q: (load[q], q))
+        lane_of[i] = j
+        load[j] += math.sqrt(sizes[i])
+    return order, lane_of
+
+
 def run_batch(args) -> None:
     """32 uneven maps: all hot-path stages per map (mesh, toplesets), then
     the batched window in one launch; beside it the same 32 maps one after
@@ -466,13 +479,7 @@ def run_batch(args) -> None:
     # only for that stream while the others run.
     side = [torch.cuda.Stream() for _ in range(8)]
     srcs = [np.ascontiguousarray(S, dtype=np.int32) for _, _, S in probs]
-    order = sorted(range(len(sizes)), key=lambda i: -sizes[i])
-    load = [0.0] * len(side)
-    lane_of = {}
-    for i in order:
-        j = min(range(len(side)), key=lambda q: load[q])
-        lane_of[i] = j
-        load[j] += math.sqrt(sizes[i])
+    order, lane_of = stream_schedule(sizes, len(side))
 
     def batched(src=dev, out_host=False):
         ready = torch.cuda.Event()
