@@ -111,12 +111,13 @@ def test_fps_graph_and_stream_paths_agree(capi):
     assert sa["iterations"] == sb["iterations"] and sa["band_updates"] == sb["band_updates"]
 
 
-@pytest.mark.parametrize("name", ["bumpy", "delaunay"])
-def test_fused_and_two_step_multi_source_agree(capi, name):
+@pytest.mark.parametrize("name,band_mode", [("bumpy", 0), ("delaunay", 0), ("bumpy", 1)])
+def test_fused_and_two_step_multi_source_agree(capi, name, band_mode):
     """Voronoi and FPS maps as one fused launch (the default) and, on a grid
     too small to split (3 CTAs), as the BFS followed by the window: the same
-    iterates, so identical distances, labels and samples.  The Delaunay mesh
-    has vertices updated from their corner lists (no ring slot)."""
+    iterates, so identical distances, labels and samples, with the adaptive
+    and the fixed band.  The Delaunay mesh has vertices updated from their
+    corner lists (no ring slot)."""
     if name == "bumpy":
         V, F = meshes.bumpy_icosphere(5, 64, 0.05, 0.1, seed=6)
     else:
@@ -126,7 +127,7 @@ def test_fused_and_two_step_multi_source_agree(capi, name):
     seeds = np.random.default_rng(7).choice(n, size=12, replace=False).astype(np.int32)
     runs = []
     for grid in (0, 3):
-        p = capi.ptp_params_default(grid=grid)
+        p = capi.ptp_params_default(grid=grid, band_mode=band_mode)
         d = torch.empty(n, dtype=torch.float32, device="cuda")
         lab = torch.empty(n, dtype=torch.int32, device="cuda")
         sv = capi.ptp_voronoi(mesh, seeds, p, d, lab)
