@@ -77,7 +77,6 @@ def main():
     t_train = time.time() - t
     # margin on held-out meshes
     Xh, Yh = learned.training_set(24, seed=1)
-    from oracle import mlp  # noqa: F401  (reference only used by the tests; here the GPU kernel infers)
     import torch
 
     wh = torch.from_numpy(w).cuda()
