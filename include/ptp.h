@@ -237,11 +237,17 @@ ptp_status ptp_distance_from_sources(ptp_mesh *mesh, const int32_t *sources, int
  * cudaFree or allocating library routine.
  *
  * Scratch: a file-scope device array sized for PTP_NOALLOC_MAX_VERTS
- * vertices (16 MiB + 256 bytes), which every GPU that loads the library holds
- * until the process exits.  A handle with more vertices is rejected with
- * PTP_ERR_TOO_LARGE.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current and caches it;
- * make that first call before any stream capture.  Every call shares the one
+ * vertices (16 MiB + 256 bytes).  It belongs to the library's device code,
+ * so every GPU on which the process uses the library holds it until the
+ * process exits, whether or not this entry point is ever called: plain
+ * ptp_distance users pay these 16 MiB per device too.  A handle with more
+ * vertices is rejected with PTP_ERR_TOO_LARGE.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current and caches it per device ordinal; make that first call
+ * before any stream capture.  The cache assumes the device's primary
+ * context (the one the CUDA runtime uses) stays alive: after
+ * cudaDeviceReset, or with another context made current, the cached
+ * address is stale and must not be used.  Every call shares the one
  * array per device and overwrites what the last call left there, so calls
  * whose work overlaps on the GPU (another stream, another host thread) race;
  * serialise them.  Arguments, results, blocking and statuses are those of

@@ -64,6 +64,18 @@ static double dot3(const double *u, const double *v) {
  * triangle is degenerate, the update falls back to the shortest edge path,
  * min(d1 + |e1|, d2 + |e2|).  With only one finite neighbour distance only
  * that edge is available; with none the result is +infinity.
+ *
+ * Evaluation.  Exact identities of this quadratic keep FP64 accurate on
+ * near-degenerate triangles (squared sine of an angle down to 1e-12), where
+ * its coefficients as written cancel: det(X^T X) = |e1 x e2|^2; (i) shift
+ * invariance -- the model's
+ * data t - d1 1 has the root p - d1, so the quadratic is solved for
+ * r = p - d1 with t' = (0, d2 - d1); (ii) the whole equation is multiplied
+ * by det = det(X^T X), i.e. Q is replaced by its adjugate
+ * M = det Q = [[c, -b], [-b, a]], which has the same roots and, det being
+ * positive, the same signs in the monotonicity condition M (t' - r 1) < 0.
+ * Without them the rounding error of the coefficients grows like
+ * (d / |e|)^2 / sin^2 of the smallest angle times the machine epsilon.
  */
 double or_update(const double *x0, const double *x1, const double *x2, double d1, double d2) {
     double e1[3], e2[3];
@@ -79,22 +91,26 @@ double or_update(const double *x0, const double *x1, const double *x2, double d1
     const double fallback = edge1 < edge2 ? edge1 : edge2;
     if (!f1 || !f2) return fallback;
 
-    const double det = a * c - b * b;
+    /* det(X^T X) = a c - b^2, computed as |e1 x e2|^2 (Lagrange's identity):
+     * the difference a c - b^2 cancels when e1 and e2 are nearly parallel */
+    const double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const double det = dot3(cr, cr);
     if (!(det > OR_DEGENERATE * a * c)) return fallback;
 
-    /* Q = (X^T X)^{-1} = [[c, -b], [-b, a]] / det */
-    const double q11 = c / det, q12 = -b / det, q22 = a / det;
-    const double qa = q11 + 2.0 * q12 + q22;                       /* 1^T Q 1     */
-    const double qb = q11 * d1 + q12 * (d1 + d2) + q22 * d2;      /* 1^T Q t     */
-    const double qc = q11 * d1 * d1 + 2.0 * q12 * d1 * d2 + q22 * d2 * d2 - 1.0; /* t^T Q t - 1 */
+    /* M = det Q = [[c, -b], [-b, a]], data t' = (0, delta) for r = p - d1 */
+    const double m11 = c, m12 = -b, m22 = a;
+    const double t1 = 0.0, t2 = d2 - d1;
+    const double qa = m11 + 2.0 * m12 + m22;                                   /* det 1^T Q 1       */
+    const double qb = m11 * t1 + m12 * (t1 + t2) + m22 * t2;                   /* det 1^T Q t'      */
+    const double qc = m11 * t1 * t1 + 2.0 * m12 * t1 * t2 + m22 * t2 * t2 - det; /* det (t'^T Q t' - 1) */
     const double disc = qb * qb - qa * qc;
     if (disc < 0.0) return fallback;
-    const double p = (qb + sqrt(disc)) / qa;
+    const double r = (qb + sqrt(disc)) / qa;
 
-    /* Q (t - p 1) < 0 componentwise */
-    const double l1 = q11 * (d1 - p) + q12 * (d2 - p);
-    const double l2 = q12 * (d1 - p) + q22 * (d2 - p);
-    if (l1 < 0.0 && l2 < 0.0) return p;
+    /* Q (t - p 1) = M (t' - r 1) / det < 0 componentwise */
+    const double l1 = m11 * (t1 - r) + m12 * (t2 - r);
+    const double l2 = m12 * (t1 - r) + m22 * (t2 - r);
+    if (l1 < 0.0 && l2 < 0.0) return d1 + r;
     return fallback;
 }
 

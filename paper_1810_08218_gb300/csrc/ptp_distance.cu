@@ -913,13 +913,83 @@ ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp
     return PTP_OK;
 }
 
-extern "C" ptp_status ptp_last_stats(ptp_toplesets_t *t, void *stream, ptp_stats *st) {
-    if (!t || !st) return PTP_ERR_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
+namespace {
+
+// Validation shared by ptp_distance and ptp_distance_noalloc.
+ptp_status check_distance_args(const ptp_toplesets_t *t, const ptp_params *params, const float *d_out) {
+    if (!t || !params || !d_out) return PTP_ERR_ARG;
+    if (!(params->eps >= 0.0) || !(params->eps_abs >= 0.0) || params->max_iter < 0 || params->trace_cap < 0)
+        return PTP_ERR_ARG;
+    if (window_block(params->block) < 0) return PTP_ERR_ARG;
+    if (params->band_mode != 0 && params->band_mode != 1) return PTP_ERR_ARG;
+    return PTP_OK;
+}
+
+// One window run of toplesets t on stream s with the given scratch: dbuf
+// holds d0, d1 (2n floats), ibuf nstamp, chg (2n ints), ctrl the control
+// block.  Clears the control block (and the trace), initialises the
+// scratch, launches the window kernel and scatters d_K to d_out.
+// ptp_distance and ptp_distance_noalloc differ only in where the scratch
+// and the control block come from.
+ptp_status run_window(const ptp_toplesets_t *t, const ptp_params *params, float *dbuf, int *ibuf, ptp_ctrl *ctrl,
+                      float *d_out, cudaStream_t s) {
+    const int64_t n = t->n;
+    const int dev = t->device;
+    const int block = window_block(params->block);
+    PTP_TRY(cudaMemsetAsync(ctrl, 0, sizeof(ptp_ctrl), s));
+    if (params->trace && params->trace_cap > 0)
+        PTP_TRY(cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s));
+    init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->off, (int)n, dbuf, dbuf + n, ibuf, ibuf + n);
+    ptp_count_launches(1);
+    PTP_TRY(cudaGetLastError());
+    int per_sm = 0;
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false>, block, 0));
+    if (per_sm < 1) return PTP_ERR_CUDA;
+    int grid = per_sm * ptp_num_sms(dev);
+    if (params->grid > 0 && params->grid < grid) grid = params->grid;
+
+    DistArgs a = {};
+    a.n = (int)n;
+    a.pos = t->pos;
+    a.ring = t->ring;
+    a.tgeom = t->tgeom;
+    a.elen = t->elen;
+    a.meta = t->meta;
+    a.row = t->row;
+    a.pairs = t->pairs;
+    a.off = t->off;
+    a.info = t->info;
+    a.d0 = dbuf;
+    a.d1 = dbuf + n;
+    a.nstamp = ibuf;
+    a.chg = ibuf + n;
+    a.ctrl = ctrl;
+    a.trace = (ptp_trace_rec *)params->trace;
+    a.trace_cap = params->trace ? params->trace_cap : 0;
+    a.eps = params->eps;
+    a.eps_abs = params->eps_abs;
+    a.max_iter = params->max_iter;
+    a.perm = nullptr;
+    a.lab0 = a.lab1 = nullptr;
+    a.band_mode = params->band_mode;
+    a.sched = params->schedule;
+    void *args[] = {(void *)&a};
+    if (params->ev_begin) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_begin, s));
+    PTP_TRY(cudaLaunchCooperativeKernel((const void *)ptp_window<false, false>, dim3(grid), dim3(block), args, 0, s));
+    ptp_count_launches(1);
+    if (params->ev_end) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_end, s));
+    scatter_out<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, dbuf, dbuf + n, ctrl, d_out);
+    ptp_count_launches(1);
+    PTP_TRY(cudaGetLastError());
+    return PTP_OK;
+}
+
+// Statistics of the run whose control block is ctrl (blocks on s).
+ptp_status read_stats(const ptp_ctrl *ctrl, const int *info_dev, cudaStream_t s, ptp_stats *st) {
     ptp_ctrl h;
     int info[4];
-    PTP_TRY(cudaMemcpyAsync(&h, t->ctrl, sizeof(ptp_ctrl), cudaMemcpyDeviceToHost, s));
-    PTP_TRY(cudaMemcpyAsync(info, t->info, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    PTP_TRY(cudaMemcpyAsync(&h, ctrl, sizeof(ptp_ctrl), cudaMemcpyDeviceToHost, s));
+    PTP_TRY(cudaMemcpyAsync(info, info_dev, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
     PTP_TRY(cudaStreamSynchronize(s));
     st->iterations = h.iterations;
     st->band_updates = h.band_updates;
@@ -932,18 +1002,13 @@ extern "C" ptp_status ptp_last_stats(ptp_toplesets_t *t, void *stream, ptp_stats
     return (ptp_status)h.status;
 }
 
+}  // namespace
+
 extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params, float *d_out, void *stream,
                                    ptp_stats *stats) {
-    if (!t || !params || !d_out) return PTP_ERR_ARG;
-    if (!(params->eps >= 0.0) || !(params->eps_abs >= 0.0) || params->max_iter < 0 || params->trace_cap < 0)
-        return PTP_ERR_ARG;
-    const int block = window_block(params->block);
-    if (block < 0) return PTP_ERR_ARG;
-    if (params->band_mode != 0 && params->band_mode != 1) return PTP_ERR_ARG;
+    PTP_CHECK(check_distance_args(t, params, d_out));
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = t->n;
-    const int dev = t->device;
-
     float *dbuf = nullptr;
     int *ibuf = nullptr;
     PTP_TRY(ptp_malloc_async((void **)&dbuf, sizeof(float) * 2 * n, s));
@@ -952,73 +1017,17 @@ extern "C" ptp_status ptp_distance(ptp_toplesets_t *t, const ptp_params *params,
         cudaFreeAsync(dbuf, s);
         return ptp_internal_cuda_status(ce);
     }
-    ptp_status st = PTP_OK;
-    do {
-        ce = cudaMemsetAsync(t->ctrl, 0, sizeof(ptp_ctrl), s);
-        if (ce != cudaSuccess) break;
-        if (params->trace && params->trace_cap > 0) {
-            ce = cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s);
-            if (ce != cudaSuccess) break;
-        }
-        init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->off, (int)n, dbuf, dbuf + n, ibuf, ibuf + n);
-        ptp_count_launches(1);
-        ce = cudaGetLastError();
-        if (ce != cudaSuccess) break;
-
-        int per_sm = 0;
-        ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false>, block, 0);
-        if (ce != cudaSuccess) break;
-        if (per_sm < 1) { st = PTP_ERR_CUDA; break; }
-        int grid = per_sm * ptp_num_sms(dev);
-        if (params->grid > 0 && params->grid < grid) grid = params->grid;
-
-        DistArgs a = {};
-        a.n = (int)n;
-        a.pos = t->pos;
-        a.ring = t->ring;
-        a.tgeom = t->tgeom;
-        a.elen = t->elen;
-        a.meta = t->meta;
-        a.row = t->row;
-        a.pairs = t->pairs;
-        a.off = t->off;
-        a.info = t->info;
-        a.d0 = dbuf;
-        a.d1 = dbuf + n;
-        a.nstamp = ibuf;
-        a.chg = ibuf + n;
-        a.ctrl = t->ctrl;
-        a.trace = (ptp_trace_rec *)params->trace;
-        a.trace_cap = params->trace ? params->trace_cap : 0;
-        a.eps = params->eps;
-        a.eps_abs = params->eps_abs;
-        a.max_iter = params->max_iter;
-        a.perm = nullptr;
-        a.lab0 = a.lab1 = nullptr;
-        a.band_mode = params->band_mode;
-        a.sched = params->schedule;
-        void *args[] = {(void *)&a};
-        if (params->ev_begin) {
-            ce = cudaEventRecord((cudaEvent_t)params->ev_begin, s);
-            if (ce != cudaSuccess) break;
-        }
-        ce = cudaLaunchCooperativeKernel((const void *)ptp_window<false, false>, dim3(grid), dim3(block), args, 0, s);
-        if (ce != cudaSuccess) break;
-        ptp_count_launches(1);
-        if (params->ev_end) {
-            ce = cudaEventRecord((cudaEvent_t)params->ev_end, s);
-            if (ce != cudaSuccess) break;
-        }
-        scatter_out<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, dbuf, dbuf + n, t->ctrl, d_out);
-        ptp_count_launches(1);
-        ce = cudaGetLastError();
-    } while (0);
+    const ptp_status st = run_window(t, params, dbuf, ibuf, t->ctrl, d_out, s);
     cudaFreeAsync(dbuf, s);
     cudaFreeAsync(ibuf, s);
-    if (ce != cudaSuccess) return ptp_internal_cuda_status(ce);
     if (st != PTP_OK) return st;
-    if (stats) return ptp_last_stats(t, stream, stats);
+    if (stats) return read_stats(t->ctrl, t->info, s, stats);
     return PTP_OK;
+}
+
+extern "C" ptp_status ptp_last_stats(ptp_toplesets_t *t, void *stream, ptp_stats *st) {
+    if (!t || !st) return PTP_ERR_ARG;
+    return read_stats(t->ctrl, t->info, (cudaStream_t)stream, st);
 }
 
 extern "C" ptp_status ptp_geodesic(const float *xyz, int64_t n_verts, const int32_t *faces, int64_t n_faces,
@@ -1081,7 +1090,9 @@ bool g_noalloc_ready[NOALLOC_MAX_DEVICES];
 
 // Device address of the scratch array for the current device.  The array's
 // name is only a host-side stand-in in host code, so its address is looked up
-// once per device, with that device current, and cached.
+// once per device, with that device current, and cached per ordinal: the
+// cache is valid as long as the device's primary context lives (not across
+// cudaDeviceReset).
 ptp_status noalloc_scratch(int dev, unsigned char **out) {
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PTP_ERR_ARG;
     if (!__atomic_load_n(&g_noalloc_ready[dev], __ATOMIC_ACQUIRE)) {
@@ -1099,12 +1110,7 @@ ptp_status noalloc_scratch(int dev, unsigned char **out) {
 
 extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params *params, float *d_out, void *stream,
                                            ptp_stats *stats) {
-    if (!t || !params || !d_out) return PTP_ERR_ARG;
-    if (!(params->eps >= 0.0) || !(params->eps_abs >= 0.0) || params->max_iter < 0 || params->trace_cap < 0)
-        return PTP_ERR_ARG;
-    const int block = window_block(params->block);
-    if (block < 0) return PTP_ERR_ARG;
-    if (params->band_mode != 0 && params->band_mode != 1) return PTP_ERR_ARG;
+    PTP_CHECK(check_distance_args(t, params, d_out));
     if (t->n > (int64_t)PTP_NOALLOC_MAX_VERTS) return PTP_ERR_TOO_LARGE;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = t->n;
@@ -1116,67 +1122,9 @@ extern "C" ptp_status ptp_distance_noalloc(ptp_toplesets_t *t, const ptp_params 
     ptp_ctrl *ctrl = (ptp_ctrl *)base;
     float *dbuf = (float *)(base + NOALLOC_HEADER);
     int *ibuf = (int *)(dbuf + 2 * n);
-
-    // the array keeps the previous call's contents: the control block must
-    // start at zero; init_distances rewrites all 4n scratch words
-    PTP_TRY(cudaMemsetAsync(ctrl, 0, sizeof(ptp_ctrl), s));
-    if (params->trace && params->trace_cap > 0)
-        PTP_TRY(cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s));
-    init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->off, (int)n, dbuf, dbuf + n, ibuf, ibuf + n);
-    ptp_count_launches(1);
-    PTP_TRY(cudaGetLastError());
-    int per_sm = 0;
-    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false>, block, 0));
-    if (per_sm < 1) return PTP_ERR_CUDA;
-    int grid = per_sm * ptp_num_sms(dev);
-    if (params->grid > 0 && params->grid < grid) grid = params->grid;
-
-    DistArgs a = {};
-    a.n = (int)n;
-    a.pos = t->pos;
-    a.ring = t->ring;
-    a.tgeom = t->tgeom;
-    a.elen = t->elen;
-    a.meta = t->meta;
-    a.row = t->row;
-    a.pairs = t->pairs;
-    a.off = t->off;
-    a.info = t->info;
-    a.d0 = dbuf;
-    a.d1 = dbuf + n;
-    a.nstamp = ibuf;
-    a.chg = ibuf + n;
-    a.ctrl = ctrl;
-    a.trace = (ptp_trace_rec *)params->trace;
-    a.trace_cap = params->trace ? params->trace_cap : 0;
-    a.eps = params->eps;
-    a.eps_abs = params->eps_abs;
-    a.max_iter = params->max_iter;
-    a.perm = nullptr;
-    a.lab0 = a.lab1 = nullptr;
-    a.band_mode = params->band_mode;
-    a.sched = params->schedule;
-    void *args[] = {(void *)&a};
-    if (params->ev_begin) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_begin, s));
-    PTP_TRY(cudaLaunchCooperativeKernel((const void *)ptp_window<false, false>, dim3(grid), dim3(block), args, 0, s));
-    ptp_count_launches(1);
-    if (params->ev_end) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_end, s));
-    scatter_out<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, dbuf, dbuf + n, ctrl, d_out);
-    ptp_count_launches(1);
-    PTP_TRY(cudaGetLastError());
+    // the array keeps the previous call's contents: run_window clears the
+    // control block and init_distances rewrites all 4n scratch words
+    PTP_CHECK(run_window(t, params, dbuf, ibuf, ctrl, d_out, s));
     if (!stats) return PTP_OK;
-    ptp_ctrl h;
-    int info[4];
-    PTP_TRY(cudaMemcpyAsync(&h, ctrl, sizeof(ptp_ctrl), cudaMemcpyDeviceToHost, s));
-    PTP_TRY(cudaMemcpyAsync(info, t->info, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
-    PTP_TRY(cudaStreamSynchronize(s));
-    stats->iterations = h.iterations;
-    stats->band_updates = h.band_updates;
-    stats->active_updates = (int64_t)h.active;
-    stats->changed = (int64_t)h.changed;
-    stats->fp64_solves = (int64_t)h.fp64;
-    stats->rho = info[0];
-    stats->status = h.status;
-    stats->checks = h.checks;
-    return (ptp_status)h.status;
+    return read_stats(ctrl, t->info, s, stats);
 }

@@ -216,6 +216,84 @@ def random_planar(n: int, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
     return V, tri.simplices.astype(np.int32)
 
 
+def _zip_rows(rows: list[tuple[np.ndarray, np.ndarray]]) -> np.ndarray:
+    """Faces stitching consecutive rows of vertices whose x increases along
+    each row: a monotone merge (zipper) walks both rows and always advances
+    the one whose next vertex lies further left, so every strip between two
+    rows is triangulated without overlap, whatever the rows' densities and
+    offsets.  `rows[r]` is (vertex indices, x positions)."""
+    F = []
+    for (li, lx), (hi_, hx) in zip(rows[:-1], rows[1:]):
+        a, b = 0, 0
+        while a < len(li) - 1 or b < len(hi_) - 1:
+            if b == len(hi_) - 1 or (a < len(li) - 1 and lx[a + 1] <= hx[b + 1]):
+                F.append((li[a], li[a + 1], hi_[b]))
+                a += 1
+            else:
+                F.append((li[a], hi_[b + 1], hi_[b]))
+                b += 1
+    return np.asarray(F, dtype=np.int32)
+
+
+def sliver_plane(nx: int = 48, bands: int = 6, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """A flat mesh full of near-degenerate triangles, built row by row over
+    [0,1] x [0,~1] and stitched by `_zip_rows`.  Between regular rows
+    (spacing h = 1/(nx-1), interior x jittered by +-0.2 h) every band adds:
+
+    * a needle row: the previous row's x positions lifted by g*h, so the
+      triangles between them have one angle of about g radians;
+    * a cap row at a gap g*h whose interior points sit at the midpoints of
+      the row below, so its triangles have one angle of about pi - 4 g;
+    * a dense row (spacing h/4) at a gap g*h above a regular row and below
+      another: the regular row's vertices then have about a dozen
+      neighbours (more than a one-ring slot holds) and needle triangles;
+
+    with g cycling through 1e-3, 1e-4, 1e-5 and 3e-6, i.e. squared sines of
+    the small angle from about 1e-6 down to 1e-11 (the smallest gaps are a
+    few float32 ulps, so the float32 positions define the slivers).  All
+    coordinates are exactly representable in float32, and consecutive rows
+    differ in float32 y."""
+    rng = np.random.default_rng(seed)
+    h = 1.0 / (nx - 1)
+    gaps = [1e-3, 1e-4, 1e-5, 3e-6]
+    base = np.linspace(0.0, 1.0, nx)
+
+    def regular():
+        x = base.copy()
+        x[1:-1] += rng.uniform(-0.2, 0.2, nx - 2) * h
+        return x
+
+    row_x: list[np.ndarray] = []
+    row_y: list[float] = []
+
+    def push(x, dy):
+        y = np.float32(0.0) if not row_y else np.float32(row_y[-1] + dy)
+        if row_y and not y > np.float32(row_y[-1]):
+            y = np.nextafter(np.float32(row_y[-1]), np.float32(np.inf))
+        row_x.append(np.asarray(x, dtype=np.float32).astype(np.float64))
+        row_y.append(float(y))
+
+    push(regular(), 0.0)
+    for b in range(bands):
+        g = gaps[b % len(gaps)]
+        push(regular(), h)
+        push(row_x[-1], g * h)                       # needles
+        push(regular(), h)
+        mid = 0.5 * (row_x[-1][:-1] + row_x[-1][1:])
+        push(np.concatenate([[0.0], mid, [1.0]]), g * h)  # caps
+        push(regular(), h)
+        push(np.linspace(0.0, 1.0, 4 * (nx - 1) + 1), g * h)  # dense, just above a regular row
+        push(regular(), h)
+        push(np.linspace(0.0, 1.0, 4 * (nx - 1) + 1), h)
+    push(regular(), h)
+    V, rows, k = [], [], 0
+    for x, y in zip(row_x, row_y):
+        rows.append((np.arange(k, k + len(x)), x))
+        V.append(np.stack([x, np.full(len(x), y), np.zeros(len(x))], axis=1))
+        k += len(x)
+    return np.concatenate(V), _zip_rows(rows)
+
+
 def random_source(n: int, seed: int) -> int:
     """A seeded uniformly random vertex index."""
     return int(np.random.default_rng(seed).integers(0, n))

@@ -186,3 +186,115 @@ def test_bounds():
             assert u > max(d1, d2) - 1e-12
             later += 1
     assert later > 100
+
+
+def _sliver(rng, sin2, where):
+    """A triangle (x0, x1, x2) in a random plane whose smallest angle has
+    squared sine sin2, at x0 (a needle pointing at the updated vertex), at
+    x1 (x0 at the blunt end of a needle) or an obtuse cap with the angle
+    pi - asin(sqrt(sin2)) at x0."""
+    th = math.asin(math.sqrt(sin2))
+    L1, L2 = rng.uniform(0.5, 2.0, size=2)
+    if where == "x0":
+        P = [(0.0, 0.0), (L1, 0.0), (L2 * math.cos(th), L2 * math.sin(th))]
+    elif where == "x1":
+        P = [(L2 * math.cos(th), L2 * math.sin(th)), (0.0, 0.0), (L1, 0.0)]
+    else:  # cap: x0 nearly on the segment x1 x2
+        P = [(0.0, 0.0), (-L1 * math.cos(th / 2), L1 * math.sin(th / 2)),
+             (L2 * math.cos(th / 2), L2 * math.sin(th / 2))]
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    t = rng.normal(size=3)
+    return [Q @ np.array([x, y, 0.0]) + t for x, y in P]
+
+
+def _textbook_update_hp(x0, x1, x2, d1, d2, mp):
+    """The update of Sec. 3.2 exactly as written -- Q = (X^T X)^{-1}, the
+    larger root of (1^T Q 1) p^2 - 2 (1^T Q t) p + (t^T Q t - 1) = 0 and the
+    test Q (t - p 1) < 0 -- evaluated in `mp` (60-digit) arithmetic from the
+    given doubles.  Returns (value, margin): margin is how far, relative to
+    the size of its terms, each decision lies from its boundary (the
+    degenerate threshold; |d2 - d1| against |x2 - x1|, where the two roots
+    meet; the two causality signs, scaled by det so their terms are edge-
+    sized), so that cases an FP64 evaluation cannot decide are skipped."""
+    X0, X1, X2 = ([mp.mpf(float(v)) for v in x] for x in (x0, x1, x2))
+    D1, D2 = mp.mpf(float(d1)), mp.mpf(float(d2))
+    e1 = [X1[i] - X0[i] for i in range(3)]
+    e2 = [X2[i] - X0[i] for i in range(3)]
+    a = sum(v * v for v in e1)
+    b = sum(e1[i] * e2[i] for i in range(3))
+    c = sum(v * v for v in e2)
+    fb = min(D1 + mp.sqrt(a), D2 + mp.sqrt(c))
+    det = a * c - b * b
+    margins = [abs(det / (a * c) / mp.mpf("1e-12") - 1)]
+    if det <= mp.mpf("1e-12") * a * c:
+        return fb, min(margins)
+    q11, q12, q22 = c / det, -b / det, a / det
+    qa = q11 + 2 * q12 + q22
+    qb = q11 * D1 + q12 * (D1 + D2) + q22 * D2
+    qc = q11 * D1 * D1 + 2 * q12 * D1 * D2 + q22 * D2 * D2 - 1
+    disc = qb * qb - qa * qc
+    A, delta = a + c - 2 * b, D2 - D1
+    margins.append(abs(A - delta * delta) / A)
+    if disc < 0:
+        return fb, min(margins)
+    p = (qb + mp.sqrt(disc)) / qa
+    l1 = q11 * (D1 - p) + q12 * (D2 - p)
+    l2 = q12 * (D1 - p) + q22 * (D2 - p)
+    r = p - D1
+    margins += [abs(l1 * det) / (abs((b - c) * r) + abs(b * delta)),
+                abs(l2 * det) / (abs((b - a) * r) + abs(a * delta))]
+    return (p if (l1 < 0 and l2 < 0) else fb), min(margins)
+
+
+def test_slivers_match_the_definition_in_high_precision():
+    """Near-degenerate triangles (smallest squared sine 1e-12 .. 1e-6, the
+    range the GPU solves in FP64; needles at x0 or at x1 and obtuse caps)
+    with linear-field and arbitrary data: the oracle's FP64 update equals
+    the textbook quadratic evaluated in 60-digit arithmetic to within
+    1e-10 of the triangle's size, away from decision boundaries.  Evaluating
+    the coefficients as written in FP64 misses this by up to 1e-3."""
+    mpmath = pytest.importorskip("mpmath")
+    mp = mpmath.mp.clone() if hasattr(mpmath.mp, "clone") else mpmath.mp
+    mp.dps = 60
+    rng = np.random.default_rng(21)
+    planar = checked = 0
+    worst = 0.0
+    for k in range(1500):
+        sin2 = 10.0 ** rng.uniform(-11.8, -6.0)
+        x0, x1, x2 = _sliver(rng, sin2, ("x0", "x1", "cap")[k % 3])
+        L = np.linalg.norm(x2 - x1)
+        scale = max(np.linalg.norm(x1 - x0), np.linalg.norm(x2 - x0))
+        base = rng.uniform(0.5, 10.0)
+        if k % 2 == 0:  # a unit in-plane linear field
+            u, w = _plane_basis(x1 - x0, x2 - x0)
+            phi = rng.uniform(0.0, 2.0 * math.pi)
+            n = math.cos(phi) * u + math.sin(phi) * w
+            d1, d2 = np.dot(n, x1) + base, np.dot(n, x2) + base
+        else:  # any difference the edge allows
+            d1 = base
+            d2 = base + rng.uniform(-0.999, 0.999) * L
+        exp, margin = _textbook_update_hp(x0, x1, x2, d1, d2, mp)
+        if margin < 1e-6:
+            continue
+        got = oracle.update(x0, x1, x2, d1, d2)
+        err = abs(got - float(exp))
+        worst = max(worst, err / scale)
+        assert err <= 1e-10 * scale, (k, sin2, got, float(exp))
+        checked += 1
+        fb = min(d1 + np.linalg.norm(x1 - x0), d2 + np.linalg.norm(x2 - x0))
+        planar += got < fb
+    assert checked > 1200 and planar > 150, (checked, planar)
+
+
+def test_needle_at_the_updated_vertex_below_the_threshold_takes_the_edge():
+    """Below the degeneracy threshold (the squared sine of the angle at x0
+    at most 1e-12) the update is the edge fallback, even for data that a
+    planar wave through the needle would fit."""
+    rng = np.random.default_rng(22)
+    for _ in range(200):
+        x0, x1, x2 = _sliver(rng, 10.0 ** rng.uniform(-16.0, -12.5), "x0")
+        target = x1 + 0.5 * (x2 - x1)
+        n = (x0 - target) / np.linalg.norm(x0 - target)
+        d1, d2 = np.dot(n, x1) + 3.0, np.dot(n, x2) + 3.0
+        fb = min(d1 + np.linalg.norm(x1 - x0), d2 + np.linalg.norm(x2 - x0))
+        assert oracle.update(x0, x1, x2, d1, d2) == pytest.approx(fb, rel=1e-14)
