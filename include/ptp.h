@@ -72,7 +72,19 @@ typedef struct ptp_params {
     int32_t grid;      /* CTAs of the window kernel; 0 = all co-resident CTAs      */
     int32_t band_mode; /* 0: the paper's dynamic band (Eq. lower_band); 1: the
                           fixed band of the complexity analysis (Sec. 6.1), lower
-                          bound ceil(k / 2), no convergence test                   */
+                          bound ceil(k / 2), no convergence test; 2: the learned
+                          multi-advance band (an extension; the paper has no
+                          counterpart): the bottom topleset is tested as in
+                          Eq. lower_band and, besides it, the toplesets above it
+                          that the learned schedule marks due are tested as one
+                          group; when both pass, the lower bound moves past all
+                          of them at once instead of by one.  A wrong prediction
+                          costs iterations, never the test.  Meant for fixpoint
+                          runs (a small eps such as 1e-7), where the result
+                          equals the dynamic band's within rounding.  Needs
+                          `schedule` (ptp_distance) or `mlp_half`
+                          (ptp_distance_from_sources); single-source entry points
+                          only                                                      */
     int32_t reserved;  /* must be 0                                                */
     void *trace;       /* optional DEVICE buffer of trace_cap ptp_trace_rec, one per
                           iteration, or NULL                                       */
@@ -80,12 +92,32 @@ typedef struct ptp_params {
     void *ev_begin;    /* optional cudaEvent_t recorded on `stream` right before the
                           window kernel, or NULL                                   */
     void *ev_end;      /* optional cudaEvent_t recorded right after it, or NULL     */
-    const int32_t *schedule; /* optional DEVICE array [rho]: for each topleset i,
-                          the number of iterations the band's lower bound is
-                          expected to stay at i (a learned schedule, see
-                          ptp_mlp_infer).  The test of Eq. lower_band is skipped
-                          until that many iterations have passed, then applied
-                          as usual every iteration.  NULL: test every iteration */
+    const int32_t *schedule; /* optional DEVICE array [rho] from ptp_mlp_infer.
+                          band_mode 0: for each topleset i, the number of
+                          iterations the band's lower bound is expected to stay
+                          at i; the test of Eq. lower_band is skipped until that
+                          many iterations have passed, then applied as usual
+                          every iteration (NULL: test every iteration).
+                          band_mode 2: for each topleset r, the iterations after
+                          it enters the band (at iteration r) until it is
+                          expected to have converged; r joins the tested group
+                          from iteration max(r + schedule[r], 32 floor(r / 32)
+                          + 33) on (the second term is when a fused launch,
+                          which infers 32 toplesets at a time, can know it)   */
+    const void *mlp_half;   /* band_mode 2 in ptp_distance_from_sources: DEVICE
+                          array of PTP_MLP_NPARAM FP16 weights of the schedule
+                          MLP.  The launch computes each topleset's window
+                          features while it copies it into topleset order and
+                          infers its schedule inside the launch, with the same
+                          arithmetic as ptp_window_features + ptp_mlp_infer, so
+                          the two paths run the same iteration                  */
+    float mlp_margin;       /* margin of that inference (see ptp_mlp_infer)       */
+    int32_t reserved2;      /* must be 0                                           */
+    int32_t *conv_trace;    /* optional DEVICE array [rho] (ptp_distance only),
+                          filled with -1 by the caller: for each topleset, the
+                          last iteration in which one of its vertices failed
+                          the relative-change test (the schedule MLP's training
+                          target)                                               */
 } ptp_params;
 
 /* One record per PTP iteration k (written only when params.trace is set). */
@@ -95,7 +127,8 @@ typedef struct ptp_trace_rec {
     int32_t active;    /* band vertices recomputed (some neighbour changed)        */
     int32_t changed;   /* band vertices whose distance changed                     */
     float maxrel;      /* max relative change over V_{i_{k-1}}                     */
-    int32_t advanced;  /* 1 if i_k = i_{k-1} + 1 (Eq. lower_band)                 */
+    int32_t advanced;  /* i_k - i_{k-1}: 1 if Eq. lower_band advanced the band,
+                          more when band_mode 2 retired a tested group          */
     double errsum;     /* FP64 sum of relative changes over V_{i_{k-1}}            */
 } ptp_trace_rec;
 

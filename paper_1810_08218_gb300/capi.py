@@ -43,7 +43,9 @@ class Params(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("eps_abs", ctypes.c_double), ("max_iter", ctypes.c_int64),
                 ("block", ctypes.c_int32), ("grid", ctypes.c_int32), ("band_mode", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64),
-                ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p), ("schedule", ctypes.c_void_p)]
+                ("ev_begin", ctypes.c_void_p), ("ev_end", ctypes.c_void_p), ("schedule", ctypes.c_void_p),
+                ("mlp_half", ctypes.c_void_p), ("mlp_margin", ctypes.c_float), ("reserved2", ctypes.c_int32),
+                ("conv_trace", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):

@@ -27,6 +27,7 @@
 
 #include "ptp_internal.cuh"
 
+#include "ptp_schedule.cuh"
 #include "ptp_update.cuh"
 
 namespace {
@@ -167,6 +168,40 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a, int *stage_smem) {
     }
 }
 
+// Learned multi-advance band in a fused launch: the schedule of toplesets
+// r0 .. r0 + 31, one per lane, from the feature sums their copies
+// accumulated (ptp_schedule.cuh) and the MLP whose FP16 weights are in `w`;
+// the sums' ring slots are cleared for reuse.  Toplesets at or past `lim`
+// (rho once known) are empty and skipped, and so is V_0 (the sources).
+__device__ __noinline__ void infer_batch(const DistArgs &a, const __half *w, int r0, int lim) {
+    const int r = r0 + (int)(threadIdx.x & 31);
+    if (r >= lim) return;
+    unsigned long long *acc = a.facc + (size_t)(r % FEAT_RING) * FEAT_WORDS;
+    if (r >= 1) {
+        const int om = __ldcg(a.off + r - 1), o0 = __ldcg(a.off + r), o1 = __ldcg(a.off + r + 1);
+        unsigned long long v[FEAT_WORDS];
+#pragma unroll
+        for (int q = 0; q < FEAT_WORDS; ++q) v[q] = __ldcg(acc + q);
+        float x[MLP_NIN], h1[MLP_H], h2[MLP_H];
+        feat_finalize(v, o1 - o0, o0 - om, r, a.n, x);
+        a.sched_w[r] = sched_from_y(mlp_forward(w, x, h1, h2), a.mlp_margin, 1 << 20);
+    }
+    // the slot serves topleset r + FEAT_RING next (V_0's sums are never used)
+#pragma unroll
+    for (int q = 0; q < FEAT_WORDS; ++q) acc[q] = 0ull;
+}
+
+// Topleset of band position p (two-step path, convergence traces only).
+__device__ __forceinline__ int topleset_of(const int *__restrict__ off, int rho, int p) {
+    int lo = 0, hi = rho;  // largest r with off[r] <= p
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldcg(off + mid) <= p) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // The persistent window kernel.  Each iteration walks the band in chunks of
 // 32 consecutive band positions (coalesced), chunk c to warp c mod W with
 // the warps numbered across CTAs first, so even a narrow band spreads over
@@ -193,8 +228,9 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a, int *stage_smem) {
 // known, which the copy of V_{k+1} needs).  rho is unknown until the BFS
 // ends; until then every window CTA has seen at least k+3 published levels,
 // so rho > k+2 and j_k = k, the same decision the known rho would give.
-template <bool PERM, bool LABELS, bool FUSED = false>
+template <bool PERM, bool LABELS, bool FUSED = false, bool MULTI = false>
 __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(DistArgs a) {
+    static_assert(!(MULTI && PERM), "the learned multi-advance band runs in topleset order");
     static_assert(!(FUSED && LABELS && !PERM), "labels are carried in the original order");
     __shared__ int2 s_queue[QUEUE_CAP];  // (vertex | in V_i << 31, bits of d_{k-1})
     if constexpr (FUSED) {
@@ -286,31 +322,63 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     // through iperm, geometry copied from the original mesh.  32-position
     // chunks are dealt to the warps from the last one down, so that in a
     // narrow band the copying warps are not the ones with band chunks.
-    auto copy_level = [&](int pb, int pe) {
+    // FUSED with the learned multi-advance band: the copy of topleset `lev`
+    // also adds its vertices' window-feature terms to the topleset's slot of
+    // the feature ring (ptp_schedule.cuh).
+    __shared__ float s_xs[3];  // the first source's position
+    auto copy_level = [&](int pb, int pe, int lev) {
         if constexpr (FUSED) {
             const int n = a.n;
             const int cb = pb & ~31;
             const int rch = pe > cb ? (pe - cb + 31) >> 5 : 0;
-            for (int c = nwarps - 1 - gwarp; c < rch; c += nwarps) {
+            constexpr bool feats = MULTI;
+            for (int c = nwarps - 1 - gwarp; c < rch; c += nwarps) {  // warp-uniform
                 const int p = cb + c * 32 + lane;
-                if (p < pb || p >= pe) continue;
-                const int v = __ldcg(a.perm + p);
-                const int4 s0 = __ldcg(a.ring_w + p), s1 = __ldcg(a.ring_w + n + p);
-                float4 g[PTP_TRI];
+                const bool have = p >= pb && p < pe;
+                FeatTerms ft = {};
+                if (have) {
+                    const int v = __ldcg(a.perm + p);
+                    const int4 s0 = __ldcg(a.ring_w + p), s1 = __ldcg(a.ring_w + n + p);
+                    float4 g[PTP_TRI];
 #pragma unroll
-                for (int q = 0; q < PTP_TRI; ++q) g[q] = __ldg(a.otgeom + (size_t)q * n + v);
-                const float4 e0 = __ldg(a.oelen + v), e1 = __ldg(a.oelen + n + v), x = __ldg(a.opos + v);
-                auto mp = [&](int id) { return id >= 0 ? __ldcg(a.iperm + id) : -1; };
-                a.ring_w[p] = make_int4(mp(s0.x), mp(s0.y), mp(s0.z), mp(s0.w));
-                a.ring_w[n + p] = make_int4(mp(s1.x), mp(s1.y), mp(s1.z), mp(s1.w));
-                a.pos_w[p] = x;
+                    for (int q = 0; q < PTP_TRI; ++q) g[q] = __ldg(a.otgeom + (size_t)q * n + v);
+                    const float4 e0 = __ldg(a.oelen + v), e1 = __ldg(a.oelen + n + v), x = __ldg(a.opos + v);
+                    const int vm = feats ? __ldcg(a.meta_w + p) : 0;
+                    auto mp = [&](int id) { return id >= 0 ? __ldcg(a.iperm + id) : -1; };
+                    a.ring_w[p] = make_int4(mp(s0.x), mp(s0.y), mp(s0.z), mp(s0.w));
+                    a.ring_w[n + p] = make_int4(mp(s1.x), mp(s1.y), mp(s1.z), mp(s1.w));
+                    a.pos_w[p] = x;
 #pragma unroll
-                for (int q = 0; q < PTP_TRI; ++q) a.tgeom_w[(size_t)q * n + p] = g[q];
-                a.elen_w[p] = e0;
-                a.elen_w[n + p] = e1;
+                    for (int q = 0; q < PTP_TRI; ++q) a.tgeom_w[(size_t)q * n + p] = g[q];
+                    a.elen_w[p] = e0;
+                    a.elen_w[n + p] = e1;
+                    if (feats) {
+                        const float el[PTP_RING] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+                        float gb[PTP_TRI];
+#pragma unroll
+                        for (int q = 0; q < PTP_TRI; ++q) gb[q] = g[q].x;
+                        ft = feat_terms(vm, el, gb, make_float3(x.x, x.y, x.z), make_float3(s_xs[0], s_xs[1], s_xs[2]),
+                                        a.feat_scale, a.feat_scale2);
+                    }
+                }
+                if (feats) feat_warp_add(a.facc + (size_t)(lev % FEAT_RING) * FEAT_WORDS, ft, have);
             }
         }
     };
+    __shared__ __half s_mlp[(FUSED && MULTI) ? MLP_NPARAM_ : 1];
+    if constexpr (FUSED && MULTI) {
+        {
+            const __half *wg = (const __half *)a.mlp_w;
+            for (int q = threadIdx.x; q < MLP_NPARAM_; q += blockDim.x) s_mlp[q] = wg[q];
+            if (threadIdx.x == 0) {
+                const float4 xs = __ldg(a.opos + __ldcg(a.perm));
+                s_xs[0] = xs.x;
+                s_xs[1] = xs.y;
+                s_xs[2] = xs.z;
+            }
+            __syncthreads();
+        }
+    }
     // barrier epochs: the topleset-ordered fused run has one more barrier,
     // after copying V_0 and V_1, so its iteration k uses epoch k + 1
     constexpr long long EP0 = (FUSED && !PERM) ? 1 : 0;
@@ -321,7 +389,8 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         }
         if constexpr (!PERM) {
             if (k == 1) {
-                copy_level(0, off_at(2));  // V_0 and V_1
+                copy_level(0, off_at(1), 0);  // V_0 and V_1
+                copy_level(off_at(1), off_at(2), 1);
                 if (ptp_grid_sync(a.ctrl->bar, 1, 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)ncta) < 0) {
                     status = PTP_ERR_TIMEOUT;
                     k = 0;
@@ -339,11 +408,23 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         bd.hi = off_at(j1 + 1);
     }
 
+    // Learned multi-advance band (band_mode 2): the group of iteration k is
+    // the toplesets V_{i+1} .. V_{gend-1} that are due (sched_due), band
+    // positions [bd.vi_end, g_hi) with g_hi = off[gend].
+    constexpr bool multi = MULTI;
+    int gend = 1, g_hi = 0;
+    const int slim = FUSED ? a.n + 8 : rho;  // entries of the schedule array
+
     for (; k >= 1 && k <= max_iter; ++k) {
         if constexpr (FUSED) {
             if (!wait_levels(need_for(k))) {
                 status = PTP_ERR_TIMEOUT;
                 break;
+            }
+            if constexpr (MULTI) {
+                // the schedule of the 32 toplesets whose features are now complete
+                if ((k % SCHED_BATCH) == SCHED_BATCH - 1 && gwarp == nwarps - 1)
+                    infer_batch(a, s_mlp, (int)k - (SCHED_BATCH - 1), rho);
             }
         }
         const int j = k < rho ? (int)k : rho - 1;
@@ -354,9 +435,9 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         const bool entering = (long long)j == k;
         const int first = bd.lo > nsrc ? bd.lo : nsrc;
         const int start = bd.copy_lo < first ? bd.copy_lo : first;
-        const bool testing = k >= check_from;
+        const bool testing = multi || k >= check_from;
 
-        int notconv = 0, n_active = 0, n_changed = 0;
+        int notconv = 0, gnotconv = 0, n_active = 0, n_changed = 0;
         float maxrel = 0.0f;
         double errsum = 0.0;
         const int base = start & ~31;
@@ -365,8 +446,8 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         // Recompute band vertex u from d_{k-1}, given its one-ring slots and
         // geometry: write d_k (and its label), stamp the neighbours if it
         // changed, and apply the relative-change test to V_{i_{k-1}}.
-        auto recompute = [&](int u, bool in_vi, float dold, int meta, int4 r0, int4 r1, float4 l0, float4 l1,
-                             const float4 *g) {
+        auto recompute = [&](int u, bool in_vi, bool in_g, float dold, int meta, int4 r0, int4 r1, float4 l0,
+                             float4 l1, const float4 *g) {
             const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
             const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
             const int m = meta & PTP_META_CNT;
@@ -387,15 +468,20 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                     for (int t = 0; t < PTP_RING; ++t)
                         if (t < m) a.nstamp[ids[t]] = (int)k;
                 }
-                if (in_vi && testing) {
+                if ((in_vi && testing) || in_g || a.conv_trace) {
                     // relative-change test of Eq. lower_band, in FP64 (the
                     // difference of two floats is exact in double)
                     const double o = dold, delta = o - (double)dnew;
-                    if (!(isfinite(o) && delta < __dadd_rn(__dmul_rn(a.eps, o), a.eps_abs))) notconv = 1;
+                    const bool fail = !(isfinite(o) && delta < __dadd_rn(__dmul_rn(a.eps, o), a.eps_abs));
+                    if (fail && in_g) gnotconv = 1;
+                    if (fail && a.conv_trace) atomicMax(a.conv_trace + topleset_of(a.off, rho, u), (int)k);
+                    if (in_vi && testing) {
+                    if (fail) notconv = 1;
                     if (a.trace) {
                         const double rel = isfinite(o) ? (o > 0.0 ? delta / o : 0.0) : (double)INF;
                         maxrel = fmaxf(maxrel, (float)rel);
                         errsum += rel;
+                    }
                     }
                 }
             }
@@ -445,7 +531,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                     dnx[u] = dold;
                     if (LABELS) lnx[u] = __ldcg(lp + u);
                 }
-                if (need) recompute(u, p < bd.vi_end, dold, meta, r0, r1, l0, l1, g);
+                if (need) recompute(u, p < bd.vi_end, multi && p >= bd.vi_end && p < g_hi, dold, meta, r0, r1, l0, l1, g);
             }
         } else {
             // chunks of this CTA's warps: c = gwarp + m * nwarps, m = 0, 1, ...
@@ -493,7 +579,9 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                             at = __shfl_sync(0xffffffffu, at, 0);
                             if (need)
                                 s_queue[at + __popc(bal & ((1u << lane) - 1u))] =
-                                    make_int2(uu[q] | (pp[q] < bd.vi_end ? (int)0x80000000 : 0), __float_as_int(dold[q]));
+                                    make_int2(uu[q] | (pp[q] < bd.vi_end ? (int)0x80000000 : 0) |
+                                                  (multi && pp[q] >= bd.vi_end && pp[q] < g_hi ? 0x40000000 : 0),
+                                              __float_as_int(dold[q]));
                         }
                     }
                 }
@@ -502,12 +590,13 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                 const int nq = s_nq;
                 for (int q = threadIdx.x; q < nq; q += blockDim.x) {
                     const int2 ent = s_queue[q];
-                    const int u = ent.x & 0x7fffffff;
+                    const int u = ent.x & 0x3fffffff;
                     int meta;
                     int4 r0, r1;
                     float4 l0, l1, g[PTP_TRI];
                     load_slots(u, meta, r0, r1, l0, l1, g);
-                    recompute(u, ent.x < 0, __int_as_float(ent.y), meta, r0, r1, l0, l1, g);
+                    recompute(u, ent.x < 0, multi && (ent.x & 0x40000000) != 0, __int_as_float(ent.y), meta, r0, r1, l0,
+                              l1, g);
                 }
                 // the queue is refilled by the next round; after the last one
                 // only in the next iteration, behind the grid barrier, so warps
@@ -518,7 +607,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         // V_{k+1} into topleset order for the next iteration, by the warps
         // counted from the last one down: in a narrow band not the band's
         // warps, in a wide one the warps with the fewest queued vertices
-        if constexpr (FUSED && !PERM) copy_level(off_at((int)k + 1), off_at((int)k + 2));
+        if constexpr (FUSED && !PERM) copy_level(off_at((int)k + 1), off_at((int)k + 2), (int)k + 1);
         tot_active += n_active;
         tot_changed += n_changed;
 
@@ -555,18 +644,31 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         const int jn = k + 1 < rho ? (int)(k + 1) : rho - 1;
         const int o_i2 = off_at(i + 2);
         const int o_jn = off_at(jn), o_jn1 = off_at(jn + 1);
-        const int sched_next = (a.sched && i + 1 < rho) ? __ldcg(a.sched + i + 1) : 1;
+        const int sched_next = (a.sched && !multi && i + 1 < rho) ? __ldcg(a.sched + i + 1) : 1;
+        // multi: what the next group end needs (schedule and offsets from gend on)
+        int pf_s[4], pf_o[5];
+        if constexpr (multi) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) pf_s[q] = gend + q < slim ? __ldcg(a.sched + gend + q) : 0x3fffffff;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) pf_o[q] = off_at(gend + q < a.n + 1 ? gend + q : a.n + 1);
+        }
 
         const int any = __syncthreads_or(notconv);
-        const long long failed = ptp_grid_sync(a.ctrl->bar, k + EP0, any ? 1u : 0u, &a.ctrl->abort, &a.ctrl->status,
-                                               prev_hi, (unsigned)ncta, PTP_WAIT_CYCLES, true);
+        const int anyg = multi ? __syncthreads_or(gnotconv) : 0;
+        const long long failed = ptp_grid_sync(a.ctrl->bar, k + EP0, (any ? 1u : 0u) | (anyg ? 0x10000u : 0u),
+                                               &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)ncta,
+                                               PTP_WAIT_CYCLES, true);
         if (failed < 0) {
             status = PTP_ERR_TIMEOUT;
             break;
         }
         // Eq. lower_band (applied from iteration check_from on), or the fixed
         // band whose lower bound is ceil(k / 2)
-        const bool advance = a.band_mode == 1 ? (int)((k + 1) >> 1) > i : (testing && failed == 0);
+        const bool bottom_ok = (failed & 0xffff) == 0, group_ok = (failed >> 16) == 0;
+        const bool advance = a.band_mode == 1 ? (int)((k + 1) >> 1) > i : (testing && bottom_ok);
+        // multi: the bottom and every due topleset above it passed: retire them all
+        const bool jump = multi && advance && gend > i + 1 && group_ok;
         if (leader) {
             band_updates += bd.hi - first;
             checks += testing ? 1 : 0;
@@ -574,10 +676,21 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                 ptp_trace_rec *rec = a.trace + (k - 1);
                 rec->i = i;
                 rec->j = j;
-                rec->advanced = advance ? 1 : 0;
+                rec->advanced = jump ? gend - i : (advance ? 1 : 0);
             }
         }
-        if (advance) {
+        if (jump) {
+            // V_{i_{k-1}} .. V_{gend-1} retire together and are copied forward
+            // in the next iteration (V_0 never changes)
+            bd.copy_lo = i >= 1 ? bd.lo : bd.vi_end;
+            i = gend;
+            if (i > rho - 1) {
+                status = PTP_OK;
+                break;
+            }
+            bd.lo = pf_o[0];
+            bd.vi_end = pf_o[1];
+        } else if (advance) {
             // i_k = i_{k-1} + 1: V_{i_{k-1}} retires and is copied forward in
             // the next iteration (V_0 never changes)
             ++i;
@@ -593,6 +706,14 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             bd.vi_end = o_i2;
         } else {
             bd.copy_lo = bd.lo;
+        }
+        if constexpr (multi) {
+            // the next group: from V_{i+1} on, every topleset due by iteration
+            // k + 1 (at most four more per iteration, from the prefetch)
+            int g = gend > i + 1 ? gend : i + 1;
+            while (g - gend < 4 && g < rho && sched_due(g, pf_s[g - gend]) <= k + 1) ++g;
+            g_hi = pf_o[g - gend];
+            gend = g;
         }
         bd.vj_beg = o_jn;
         bd.hi = o_jn1;
@@ -775,8 +896,8 @@ __global__ void fused_gather(const ptp_ctrl *__restrict__ ctrl, int n, const int
 
 // The fused window kernel: renumbered (topleset order, the single-map
 // path) or in the original order (multi-source maps, with or without labels).
-const void *fused_kernel(bool perm, bool labels) {
-    if (!perm) return (const void *)ptp_window<false, false, true>;
+const void *fused_kernel(bool perm, bool labels, bool multi) {
+    if (!perm) return multi ? (const void *)ptp_window<false, false, true, true> : (const void *)ptp_window<false, false, true>;
     return labels ? (const void *)ptp_window<true, true, true> : (const void *)ptp_window<true, false, true>;
 }
 
@@ -795,7 +916,8 @@ ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int m, bo
     *block = window_block(params->block);
     if (*block < 0) return PTP_ERR_ARG;
     int per_sm = 0;
-    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel(perm, labels), *block, 0));
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel(perm, labels, params->band_mode == 2),
+                                                          *block, 0));
     if (per_sm < 1) return PTP_ERR_CUDA;
     *grid = per_sm * ptp_num_sms(mesh->device);
     if (params->grid > 0 && params->grid < *grid) *grid = params->grid;
@@ -886,7 +1008,21 @@ ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp
     a.max_iter = params->max_iter;
     a.perm = b->queue;
     a.band_mode = params->band_mode;
-    a.sched = nullptr;  // a schedule needs the whole toplesets first
+    a.sched = nullptr;  // band_mode 0: a schedule needs the whole toplesets first
+    const bool multi = params->band_mode == 2;
+    if (multi) {
+        // the learned multi-advance band: the launch infers the schedule
+        if (perm || !rb->sched || !rb->facc || !params->mlp_half) return PTP_ERR_ARG;
+        PTP_TRY(cudaMemsetAsync(rb->facc, 0, sizeof(unsigned long long) * FEAT_RING * FEAT_WORDS, s));
+        a.sched = rb->sched;
+        a.sched_w = rb->sched;
+        a.facc = rb->facc;
+        a.mlp_w = params->mlp_half;
+        a.mlp_margin = params->mlp_margin;
+        const double diam = mesh->diameter > 0.0 ? mesh->diameter : 1.0;
+        a.feat_scale = 1073741824.0 / diam;
+        a.feat_scale2 = 1073741824.0 / (diam * diam);
+    }
     a.producers = producers;
     a.level = b->level;
     a.queue_w = b->queue;
@@ -907,7 +1043,7 @@ ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp
         PTP_TRY(cudaMemsetAsync(params->trace, 0, sizeof(ptp_trace_rec) * params->trace_cap, s));
     void *args[] = {(void *)&a};
     if (params->ev_begin) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_begin, s));
-    PTP_TRY(cudaLaunchCooperativeKernel(fused_kernel(perm, labels), dim3(grid), dim3(block), args, 0, s));
+    PTP_TRY(cudaLaunchCooperativeKernel(fused_kernel(perm, labels, multi), dim3(grid), dim3(block), args, 0, s));
     ptp_count_launches(1);
     if (params->ev_end) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_end, s));
     return PTP_OK;
@@ -921,7 +1057,10 @@ ptp_status check_distance_args(const ptp_toplesets_t *t, const ptp_params *param
     if (!(params->eps >= 0.0) || !(params->eps_abs >= 0.0) || params->max_iter < 0 || params->trace_cap < 0)
         return PTP_ERR_ARG;
     if (window_block(params->block) < 0) return PTP_ERR_ARG;
-    if (params->band_mode != 0 && params->band_mode != 1) return PTP_ERR_ARG;
+    if (params->band_mode < 0 || params->band_mode > 2) return PTP_ERR_ARG;
+    if (params->band_mode == 2 && !params->schedule) return PTP_ERR_ARG;  // the learned band needs its schedule
+    if (params->reserved != 0 || params->reserved2 != 0 || params->mlp_half) return PTP_ERR_ARG;
+    if (t->n >= 0x40000000) return PTP_ERR_TOO_LARGE;  // queue entries carry two flag bits
     return PTP_OK;
 }
 
@@ -942,8 +1081,10 @@ ptp_status run_window(const ptp_toplesets_t *t, const ptp_params *params, float 
     init_distances<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->off, (int)n, dbuf, dbuf + n, ibuf, ibuf + n);
     ptp_count_launches(1);
     PTP_TRY(cudaGetLastError());
+    const void *fn = params->band_mode == 2 ? (const void *)ptp_window<false, false, false, true>
+                                            : (const void *)ptp_window<false, false>;
     int per_sm = 0;
-    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ptp_window<false, false>, block, 0));
+    PTP_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0));
     if (per_sm < 1) return PTP_ERR_CUDA;
     int grid = per_sm * ptp_num_sms(dev);
     if (params->grid > 0 && params->grid < grid) grid = params->grid;
@@ -973,9 +1114,10 @@ ptp_status run_window(const ptp_toplesets_t *t, const ptp_params *params, float 
     a.lab0 = a.lab1 = nullptr;
     a.band_mode = params->band_mode;
     a.sched = params->schedule;
+    a.conv_trace = params->conv_trace;
     void *args[] = {(void *)&a};
     if (params->ev_begin) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_begin, s));
-    PTP_TRY(cudaLaunchCooperativeKernel((const void *)ptp_window<false, false>, dim3(grid), dim3(block), args, 0, s));
+    PTP_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, s));
     ptp_count_launches(1);
     if (params->ev_end) PTP_TRY(cudaEventRecord((cudaEvent_t)params->ev_end, s));
     scatter_out<<<blocks_for(n, 256, dev), 256, 0, s>>>(t->perm, (int)n, dbuf, dbuf + n, ctrl, d_out);

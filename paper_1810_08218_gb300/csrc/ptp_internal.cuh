@@ -156,7 +156,12 @@ struct ptp_renum_bufs {
     float4 *tgeom;  // [PTP_TRI n]
     float4 *elen;   // [2 n]
     int *iperm;     // [n] original vertex -> position
+    // learned multi-advance band (band_mode 2) only, else NULL:
+    int *sched;                // [n + 8] schedule the launch infers, per topleset
+    unsigned long long *facc;  // [PTP_FEAT_RING_WORDS] ring of per-topleset window-feature sums
 };
+// Words of that ring (64 toplesets x 8; ptp_schedule.cuh)
+#define PTP_FEAT_RING_WORDS 512
 // perm: the window runs in the original order (multi-source maps; with
 // labels, Voronoi regions) and rb needs only meta, ring and iperm (the BFS
 // records); otherwise the renumbered single-map path (d by position).

@@ -1,36 +1,30 @@
-// Learned iteration schedule: a small MLP (6 -> 32 -> 32 -> 1, FP16 weights,
-// FP32 accumulation) predicts, for every topleset window V_i, how many
-// iterations the band's lower bound stays at i.  The window kernel then runs
-// that many iterations without the relative-change test of Eq. lower_band,
-// tests once, and falls back to tested iterations if V_i has not converged,
-// so with predictions that do not exceed the plain method's counts the
-// result is the plain method's.  The paper notes that the iterations needed
-// grow as the toplesets diverge from the distance isocurves (Sec. 5.2); the
-// features describe that per window.
+// Learned window schedule: a small MLP (6 -> 32 -> 32 -> 1, FP16 weights,
+// FP32 accumulation) predicts, for every topleset window V_r, the log2 of the
+// number of iterations after it enters the band (at iteration r) until it has
+// converged.  The window kernel uses the prediction in the learned
+// multi-advance band (band_mode 2): toplesets whose predicted time has come
+// are tested as one group besides the bottom topleset of Eq. lower_band, and
+// when both pass the band's lower bound moves past all of them at once.  The
+// paper notes that the iterations needed grow as the toplesets diverge from
+// the distance isocurves (Sec. 5.2); the features describe that per window
+// (ptp_schedule.cuh).  In band_mode 0 a schedule only delays the first test
+// of each bottom topleset.
 //
-// Window features (per topleset r, computed on the device):
-//   0: log2(|V_r| + 1) / 20                       vertex count
-//   1: mean ring-edge length over V_r / mesh mean  edge-length mean
-//   2: std of those lengths / mesh mean            edge-length std
-//   3: smallest triangle angle at V_r's vertices   minimum angle (radians)
-//   4: std / mean of |x - x_s| over V_r, x_s the   front spread: how far the
-//      first source                                topleset is from a sphere
-//   5: r / rho                                     window position
-//
-// Parameters, one flat FP32 array (MLP_NPARAM): W1[32][6], b1[32],
-// W2[32][32], b2[32], W3[32], b3.
+// This file: the features of a toplesets handle, inference, and training
+// (fused forward + backward, Adam).  Parameters, one flat FP32 array
+// (PTP_MLP_NPARAM): W1[32][6], b1[32], W2[32][32], b2[32], W3[32], b3.
 #include <cuda_fp16.h>
 #include <math.h>
 
 #include "ptp_internal.cuh"
+#include "ptp_schedule.cuh"
 
 namespace {
 
-constexpr int H = 32;
-constexpr int NIN = 6;
-constexpr int OW1 = 0, OB1 = OW1 + H * NIN, OW2 = OB1 + H, OB2 = OW2 + H * H, OW3 = OB2 + H, OB3 = OW3 + H;
-constexpr int NPARAM = OB3 + 1;
-static_assert(NPARAM == PTP_MLP_NPARAM, "parameter count");
+constexpr int H = MLP_H;
+constexpr int NIN = MLP_NIN;
+constexpr int OW1 = MLP_OW1, OB1 = MLP_OB1, OW2 = MLP_OW2, OB2 = MLP_OB2, OW3 = MLP_OW3, OB3 = MLP_OB3;
+constexpr int NPARAM = MLP_NPARAM_;
 
 unsigned blocks_for(int64_t work, int threads, int device) {
     int64_t b = (work + threads - 1) / threads;
@@ -50,99 +44,57 @@ __device__ __forceinline__ int level_of(const int *__restrict__ off, int rho, in
     return lo;
 }
 
-// Per-topleset sums: acc[r] = {count, sum e, sum e^2, sum rad, sum rad^2,
-// min angle bits, pad, pad}; acc[n] holds the mesh's edge sum and count.
+// Per-topleset sums of the window features (ptp_schedule.cuh):
+// acc[r * FEAT_WORDS ...], the same integers the fused launch accumulates
+// while it copies each topleset.  A warp's positions are consecutive, so its
+// lanes are grouped by topleset and each group adds its sums once.
 __global__ void window_sums(int n, const int *__restrict__ off, const int *__restrict__ info,
                             const float4 *__restrict__ pos, const int *__restrict__ meta,
-                            const float4 *__restrict__ tgeom, const float4 *__restrict__ elen, float *__restrict__ acc) {
+                            const float4 *__restrict__ tgeom, const float4 *__restrict__ elen, double scale,
+                            double scale2, unsigned long long *__restrict__ acc) {
     const int rho = info[0];
     const int reached = info[1];
-    const float4 xs = pos[0];  // V_0 comes first: a source
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < reached; u += gridDim.x * blockDim.x) {
-        const int r = level_of(off, rho, u);
-        const int m = __ldg(meta + u);
-        const int cnt = (m & PTP_META_GENERAL) ? 0 : (m & PTP_META_CNT);
-        const float4 l0 = __ldg(elen + u), l1 = __ldg(elen + n + u);
-        const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
-        float es = 0.0f, eq = 0.0f, amin = 3.14159265f;
+    const float4 s0 = pos[0];  // V_0 comes first: a source
+    const float3 xs = make_float3(s0.x, s0.y, s0.z);
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < reached; base += stride) {
+        const int u = base + lane;
+        const bool ok = u < reached;
+        int r = -1;
+        FeatTerms f = {};
+        if (ok) {
+            r = level_of(off, rho, u);
+            const float4 l0 = __ldg(elen + u), l1 = __ldg(elen + n + u);
+            const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+            float gb[PTP_TRI];
 #pragma unroll
-        for (int t = 0; t < PTP_RING; ++t) {
-            if (t < cnt) {
-                es += el[t];
-                eq += el[t] * el[t];
-            }
+            for (int t = 0; t < PTP_TRI; ++t) gb[t] = __ldg(tgeom + (size_t)t * n + u).x;
+            const float4 p = __ldg(pos + u);
+            f = feat_terms(__ldg(meta + u), el, gb, make_float3(p.x, p.y, p.z), xs, scale, scale2);
         }
-#pragma unroll
-        for (int t = 0; t < PTP_TRI; ++t) {
-            if (t < cnt - 1) {
-                const float4 g = __ldg(tgeom + (size_t)t * n + u);
-                const float den = el[t] * el[t + 1];
-                if (den > 0.0f) amin = fminf(amin, acosf(fmaxf(-1.0f, fminf(1.0f, g.x / den))));
-            }
+        bool todo = ok;
+        while (__any_sync(0xffffffffu, todo)) {  // warp-uniform
+            const int lead = __ffs(__ballot_sync(0xffffffffu, todo)) - 1;
+            const int rl = __shfl_sync(0xffffffffu, r, lead);
+            const bool mine = todo && r == rl;
+            feat_warp_add(acc + (size_t)rl * FEAT_WORDS, f, mine);
+            todo = todo && !mine;
         }
-        const float4 p = pos[u];
-        const float dx = p.x - xs.x, dy = p.y - xs.y, dz = p.z - xs.z;
-        const float rad = sqrtf(dx * dx + dy * dy + dz * dz);
-        float *a = acc + (size_t)r * 8;
-        atomicAdd(a + 0, 1.0f);
-        atomicAdd(a + 1, es);
-        atomicAdd(a + 2, eq);
-        atomicAdd(a + 3, rad);
-        atomicAdd(a + 4, rad * rad);
-        atomicMin((int *)(a + 5), __float_as_int(amin));
-        atomicAdd(a + 6, (float)cnt);
-        atomicAdd(acc + (size_t)n * 8 + 0, es);
-        atomicAdd(acc + (size_t)n * 8 + 1, (float)cnt);
     }
 }
 
-__global__ void init_sums(int n, float *acc) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 8 * (n + 1); i += gridDim.x * blockDim.x)
-        acc[i] = (i % 8 == 5) ? 3.14159265f : 0.0f;
-}
-
-__global__ void window_finalize(int n, const int *__restrict__ info, const float *__restrict__ acc,
-                                float *__restrict__ feat) {
+__global__ void window_finalize(int n, const int *__restrict__ off, const int *__restrict__ info,
+                                const unsigned long long *__restrict__ acc, float *__restrict__ feat) {
     const int rho = info[0];
-    const float emean = acc[(size_t)n * 8 + 0] / fmaxf(acc[(size_t)n * 8 + 1], 1.0f);
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rho; r += gridDim.x * blockDim.x) {
-        const float *a = acc + (size_t)r * 8;
-        const float c = a[0], ne = fmaxf(a[6], 1.0f);
-        const float em = a[1] / ne;
-        const float ev = fmaxf(a[2] / ne - em * em, 0.0f);
-        const float rm = a[3] / fmaxf(c, 1.0f);
-        const float rv = fmaxf(a[4] / fmaxf(c, 1.0f) - rm * rm, 0.0f);
-        float *f = feat + (size_t)r * NIN;
-        f[0] = log2f(c + 1.0f) / 20.0f;
-        f[1] = emean > 0.0f ? em / emean : 0.0f;
-        f[2] = emean > 0.0f ? sqrtf(ev) / emean : 0.0f;
-        f[3] = a[5];
-        f[4] = rm > 0.0f ? sqrtf(rv) / rm : 0.0f;
-        f[5] = (float)r / (float)(rho > 1 ? rho : 1);
-    }
-}
-
-// Forward pass of one sample with FP16 weights from shared memory and FP32
-// accumulation; keeps the hidden activations for the backward pass.
-__device__ __forceinline__ float mlp_forward(const __half *w, const float x[NIN], float h1[H], float h2[H]) {
-#pragma unroll 4
-    for (int j = 0; j < H; ++j) {
-        float z = __half2float(w[OB1 + j]);
+        const int count = off[r + 1] - off[r];
+        const int prev = r > 0 ? off[r] - off[r - 1] : 1;
+        float x[NIN];
+        feat_finalize(acc + (size_t)r * FEAT_WORDS, count, prev, r, n, x);
 #pragma unroll
-        for (int i = 0; i < NIN; ++i) z = fmaf(__half2float(w[OW1 + j * NIN + i]), x[i], z);
-        h1[j] = fmaxf(z, 0.0f);
+        for (int q = 0; q < NIN; ++q) feat[(size_t)r * NIN + q] = x[q];
     }
-#pragma unroll 4
-    for (int j = 0; j < H; ++j) {
-        float z = __half2float(w[OB2 + j]);
-#pragma unroll
-        for (int i = 0; i < H; ++i) z = fmaf(__half2float(w[OW2 + j * H + i]), h1[i], z);
-        h2[j] = fmaxf(z, 0.0f);
-    }
-    float y = __half2float(w[OB3]);
-#pragma unroll
-    for (int i = 0; i < H; ++i) y = fmaf(__half2float(w[OW3 + i]), h2[i], y);
-    return y;
 }
 
 __global__ void __launch_bounds__(256) mlp_infer(const __half *__restrict__ wh, const float *__restrict__ feat,
@@ -156,10 +108,7 @@ __global__ void __launch_bounds__(256) mlp_infer(const __half *__restrict__ wh, 
         float x[NIN], h1[H], h2[H];
 #pragma unroll
         for (int i = 0; i < NIN; ++i) x[i] = feat[(size_t)s * NIN + i];
-        const float y = mlp_forward(w, x, h1, h2);
-        const float nh = exp2f(fminf(y - margin, 24.0f));
-        int v = nh >= 1.0f ? (int)nh : 1;
-        sched[s] = v < cap ? v : cap;
+        sched[s] = sched_from_y(mlp_forward(w, x, h1, h2), margin, cap);
     }
 }
 
@@ -248,14 +197,19 @@ extern "C" ptp_status ptp_window_features(ptp_toplesets_t *t, float *feat_out, v
     if (!t || !feat_out) return PTP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)t->n;
-    float *acc = nullptr;
-    PTP_TRY(ptp_malloc_async((void **)&acc, sizeof(float) * 8 * ((size_t)n + 1), s));
-    init_sums<<<blocks_for(8 * ((int64_t)n + 1), 256, t->device), 256, 0, s>>>(n, acc);
-    window_sums<<<blocks_for(n, 256, t->device), 256, 0, s>>>(n, t->off, t->info, t->pos, t->meta, t->tgeom, t->elen,
-                                                              acc);
-    window_finalize<<<blocks_for(n, 256, t->device), 256, 0, s>>>(n, t->info, acc, feat_out);
-    ptp_count_launches(3);
-    const cudaError_t e = cudaGetLastError();
+    unsigned long long *acc = nullptr;
+    const size_t bytes = sizeof(unsigned long long) * FEAT_WORDS * ((size_t)n + 1);
+    PTP_TRY(ptp_malloc_async((void **)&acc, bytes, s));
+    cudaError_t e = cudaMemsetAsync(acc, 0, bytes, s);
+    if (e == cudaSuccess) {
+        const double diam = t->mesh->diameter > 0.0 ? t->mesh->diameter : 1.0;
+        window_sums<<<blocks_for(n, 256, t->device), 256, 0, s>>>(n, t->off, t->info, t->pos, t->meta, t->tgeom,
+                                                                  t->elen, 1073741824.0 / diam,
+                                                                  1073741824.0 / (diam * diam), acc);
+        window_finalize<<<blocks_for(n, 256, t->device), 256, 0, s>>>(n, t->off, t->info, acc, feat_out);
+        ptp_count_launches(2);
+        e = cudaGetLastError();
+    }
     cudaFreeAsync(acc, s);
     return e == cudaSuccess ? PTP_OK : ptp_internal_cuda_status(e);
 }

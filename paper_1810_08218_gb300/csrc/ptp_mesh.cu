@@ -46,6 +46,10 @@ extern "C" ptp_status ptp_params_default(ptp_params *p) {
     p->ev_begin = nullptr;
     p->ev_end = nullptr;
     p->schedule = nullptr;
+    p->mlp_half = nullptr;
+    p->mlp_margin = 0.0f;
+    p->reserved2 = 0;
+    p->conv_trace = nullptr;
     return PTP_OK;
 }
 

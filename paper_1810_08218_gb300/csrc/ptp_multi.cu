@@ -157,12 +157,15 @@ struct RenumAlloc {
     cudaStream_t s = nullptr;
     // records_only: just what the BFS CTAs of an original-order run write
     // (meta, slots, iperm)
-    ptp_status alloc(int n, cudaStream_t st, bool records_only = false) {
+    // multi: also the schedule and feature sums of the learned multi-advance band
+    ptp_status alloc(int n, cudaStream_t st, bool records_only = false, bool multi = false) {
         s = st;
         const size_t N = (size_t)n;
         const size_t R = records_only ? 0 : N;
         const size_t parts[] = {sizeof(float4) * R, sizeof(int4) * 2 * N, sizeof(int) * N,
-                                sizeof(float4) * PTP_TRI * R, sizeof(float4) * 2 * R, sizeof(int) * N};
+                                sizeof(float4) * PTP_TRI * R, sizeof(float4) * 2 * R, sizeof(int) * N,
+                                multi ? sizeof(int) * (N + 8) : 0,
+                                multi ? sizeof(unsigned long long) * PTP_FEAT_RING_WORDS : 0};
         size_t bytes = 0;
         for (size_t z : parts) bytes += (z + 255) & ~(size_t)255;
         PTP_TRY(ptp_malloc_async(&base, bytes, st));
@@ -179,6 +182,8 @@ struct RenumAlloc {
         rb.tgeom = (float4 *)take();
         rb.elen = (float4 *)take();
         rb.iperm = (int *)take();
+        rb.sched = multi ? (int *)take() : nullptr;
+        rb.facc = multi ? (unsigned long long *)take() : nullptr;
         return PTP_OK;
     }
     ~RenumAlloc() {
@@ -186,10 +191,14 @@ struct RenumAlloc {
     }
 };
 
-ptp_status check_params(const ptp_params *p) {
+// allow_multi: the entry point runs the learned multi-advance band (band_mode 2)
+ptp_status check_params(const ptp_params *p, bool allow_multi = false) {
     if (!p) return PTP_ERR_ARG;
     if (!(p->eps >= 0.0) || !(p->eps_abs >= 0.0) || p->max_iter < 0 || p->trace_cap < 0) return PTP_ERR_ARG;
-    if (p->band_mode != 0 && p->band_mode != 1) return PTP_ERR_ARG;
+    if (p->reserved != 0 || p->reserved2 != 0 || p->conv_trace) return PTP_ERR_ARG;
+    if (p->band_mode == 2 ? !(allow_multi && p->mlp_half && !p->schedule) : (p->band_mode != 0 && p->band_mode != 1))
+        return PTP_ERR_ARG;
+    if (p->band_mode != 2 && p->mlp_half) return PTP_ERR_ARG;
     if (p->block != 0 && (p->block < 64 || p->block > 512 || p->block % 32 != 0)) return PTP_ERR_ARG;
     return PTP_OK;
 }
@@ -211,8 +220,10 @@ extern "C" ptp_status ptp_distance_from_sources(ptp_mesh *mesh, const int32_t *s
                                                const ptp_params *params, float *d_out, void *stream,
                                                ptp_stats *stats) {
     if (!mesh || !sources || m < 1 || !d_out || (ptr_kind != PTP_HOST && ptr_kind != PTP_DEVICE)) return PTP_ERR_ARG;
-    PTP_CHECK(check_params(params));
+    PTP_CHECK(check_params(params, true));
     if (params->schedule) return PTP_ERR_ARG;
+    const bool multi = params->band_mode == 2;
+    if (multi && mesh->n >= 0x40000000) return PTP_ERR_TOO_LARGE;  // queue entries carry two flag bits
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)mesh->n;
     std::vector<int32_t> h((size_t)m);
@@ -234,9 +245,12 @@ extern "C" ptp_status ptp_distance_from_sources(ptp_mesh *mesh, const int32_t *s
     if (ptp_internal_fused_producers(mesh, params, m, false, false) > 0) {
         // topleset-ordered copy written during the launch (200 B per vertex)
         RenumAlloc ra;
-        PTP_CHECK(ra.alloc(n, s));
+        PTP_CHECK(ra.alloc(n, s, false, multi));
         PTP_CHECK(ptp_internal_fused(mesh, &ma.b, params, src, nullptr, m, false, false, &ra.rb, s));
         PTP_CHECK(ptp_internal_fused_gather(mesh, &ma.b, &ra.rb, d_out, s));
+    } else if (multi) {
+        // the learned band infers its schedule inside the split launch
+        return PTP_ERR_ARG;
     } else {
         // too few CTAs to split the launch: BFS, then the window in the original order
         PTP_CHECK(ptp_internal_bfs(mesh, &ma.b, src, nullptr, m, s));

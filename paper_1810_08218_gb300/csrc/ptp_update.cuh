@@ -66,6 +66,13 @@ struct DistArgs {
     int *iperm;
     const int *gmap;  // renumbered fused launch: original vertex -> position for the corner lists (= iperm)
     int coherent;     // the renumbered arrays are written during the launch: load them through L2
+    // learned multi-advance band (band_mode 2; sched above is then the due delays)
+    int *sched_w;                  // fused: the schedule the launch infers, one entry per topleset
+    unsigned long long *facc;      // fused: ring of per-topleset feature sums (ptp_schedule.cuh)
+    const void *mlp_w;             // fused: FP16 MLP weights
+    float mlp_margin;
+    double feat_scale, feat_scale2;  // 2^30 / diameter and its square over the diameter
+    int *conv_trace;               // optional [rho]: last iteration a topleset failed the test
 };
 
 __device__ __forceinline__ float fsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
