@@ -201,6 +201,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the oracle's map at stored sample vertices, for maps too large for the
+# CPU-baseline leg to run whole
+STORED_SAMPLES = {"terrain_4096": os.path.join(ROOT, "tests", "golden", "terrain_4096_oracle_eps1e-3.txt")}
+
 # one full oracle map takes about this long on one host core; larger maps are
 # timed on a bounded prefix of their iterations (the CPU baseline leg)
 CPU_BASELINE_BUDGET_S = 30.0
@@ -225,13 +229,16 @@ def cpu_oracle_full_map(workload: str, V=None, F=None, S=None) -> tuple[dict, np
         return ({"value": round(dt * 1e3, 3), "unit": "ms per map", "cores": 1, "kind": "oracle",
                  "sample": f"one full map of the workload on 1 host core (K={r.K}, {r.updates} vertex updates, "
                            f"{dt:.1f} s)"}, r.d)
-    # a prefix of about CPU_BASELINE_BUDGET_S or less: a map this large no
-    # longer fits the host's caches and costs ~600 ns per update (measured on
-    # the 4096^2 terrain), against ~150 ns for the 1M torus
-    m_iter = max(1, int(counts["K"] * CPU_BASELINE_BUDGET_S / (counts["updates"] * 600e-9)))
-    t = time.perf_counter()
-    r = oracle.ptp(V, F, S, eps=1e-3, max_iter=m_iter)
-    dt = time.perf_counter() - t
+    # a prefix of the map's iterations, doubled until it takes a third of
+    # the budget (early iterations have narrow bands and cost little)
+    m_iter = max(1, counts["K"] // 32)
+    while True:
+        t = time.perf_counter()
+        r = oracle.ptp(V, F, S, eps=1e-3, max_iter=m_iter)
+        dt = time.perf_counter() - t
+        if dt >= CPU_BASELINE_BUDGET_S / 3 or m_iter >= counts["K"]:
+            break
+        m_iter = min(2 * m_iter, counts["K"])
     ms = dt * 1e3 * counts["updates"] / r.updates
     return ({"value": round(ms, 3), "unit": "ms per map", "cores": 1, "kind": "oracle",
              "sample": f"the first {m_iter} of the map's {counts['K']} iterations on 1 host core ({r.updates} of "
@@ -310,6 +317,18 @@ def map_accuracy(workload: str, d_gpu: np.ndarray, V32: np.ndarray, S, d_oracle)
     if d_oracle is not None:
         fin = np.isfinite(d_oracle)
         out["max_abs_dd_over_diam_vs_oracle"] = float(np.max(np.abs(g[fin] - d_oracle[fin])) / diam)
+        out["tolerance_over_diam"] = 1e-5
+    elif workload in STORED_SAMPLES and os.path.exists(STORED_SAMPLES[workload]):
+        # a map too large for the CPU-baseline leg: the oracle's values stored
+        # at seeded sample vertices (tests/golden, written offline)
+        idx, val = [], []
+        for line in open(STORED_SAMPLES[workload]):
+            if not line.startswith("#"):
+                a, b = line.split()
+                idx.append(int(a))
+                val.append(float(b))
+        out["max_abs_dd_over_diam_vs_oracle"] = float(np.max(np.abs(g[np.array(idx)] - np.array(val))) / diam)
+        out["oracle_samples"] = len(idx)
         out["tolerance_over_diam"] = 1e-5
     exact = accuracy._exact(workload, V32.astype(np.float64), np.asarray(S))
     if exact is not None:

@@ -102,7 +102,7 @@ typedef struct ptp_params {
                           it enters the band (at iteration r) until it is
                           expected to have converged; r joins the tested group
                           from iteration max(r + schedule[r], 32 floor(r / 32)
-                          + 33) on (the second term is when a fused launch,
+                          + 34) on (the second term is when a fused launch,
                           which infers 32 toplesets at a time, can know it)   */
     const void *mlp_half;   /* band_mode 2 in ptp_distance_from_sources: DEVICE
                           array of PTP_MLP_NPARAM FP16 weights of the schedule

@@ -168,27 +168,71 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a, int *stage_smem) {
     }
 }
 
-// Learned multi-advance band in a fused launch: the schedule of toplesets
-// r0 .. r0 + 31, one per lane, from the feature sums their copies
-// accumulated (ptp_schedule.cuh) and the MLP whose FP16 weights are in `w`;
-// the sums' ring slots are cleared for reuse.  Toplesets at or past `lim`
-// (rho once known) are empty and skipped, and so is V_0 (the sources).
-__device__ __noinline__ void infer_batch(const DistArgs &a, const __half *w, int r0, int lim) {
-    const int r = r0 + (int)(threadIdx.x & 31);
+// Learned multi-advance band in a fused launch: the schedule of topleset r
+// (one warp), from the feature sums its copy accumulated (ptp_schedule.cuh)
+// and the MLP whose FP16 weights are in `w`; the sums' ring slot is cleared
+// for reuse.  Toplesets at or past `lim` (rho once known) are empty and
+// skipped, and V_0 (the sources) needs no schedule.
+__device__ __noinline__ void infer_one(const DistArgs &a, const __half *w, int r, int lim) {
     if (r >= lim) return;
+    const int lane = threadIdx.x & 31;
     unsigned long long *acc = a.facc + (size_t)(r % FEAT_RING) * FEAT_WORDS;
     if (r >= 1) {
         const int om = __ldcg(a.off + r - 1), o0 = __ldcg(a.off + r), o1 = __ldcg(a.off + r + 1);
         unsigned long long v[FEAT_WORDS];
 #pragma unroll
         for (int q = 0; q < FEAT_WORDS; ++q) v[q] = __ldcg(acc + q);
-        float x[MLP_NIN], h1[MLP_H], h2[MLP_H];
+        float x[MLP_NIN];
         feat_finalize(v, o1 - o0, o0 - om, r, a.n, x);
-        a.sched_w[r] = sched_from_y(mlp_forward(w, x, h1, h2), a.mlp_margin, 1 << 20);
+        const float y = mlp_forward_warp(w, x);
+        if (lane == 0) a.sched_w[r] = sched_from_y(y, a.mlp_margin, 1 << 20);
     }
+    __syncwarp();
     // the slot serves topleset r + FEAT_RING next (V_0's sums are never used)
+    if (lane < FEAT_WORDS) acc[lane] = 0ull;
+}
+
+// Learned multi-advance band in a fused launch: the window-feature sums of
+// toplesets r0 .. r0 + 31 (copied into topleset order in earlier iterations;
+// boff[t] = off[r0 + t]) into their slots of the feature ring, by every warp
+// of the window CTAs at once.  Kept out of line: it runs once every
+// SCHED_BATCH iterations and must not add to the iteration's registers.
+__device__ __noinline__ void feature_pass(const DistArgs &a, int r0, int gwarp, int nwarps, const int *boff,
+                                          const float *xs3) {
+    const int lane = threadIdx.x & 31;
+    const int pb = boff[0], pe = boff[SCHED_BATCH];
+    const int cb = pb & ~31;
+    const int rch = pe > cb ? (pe - cb + 31) >> 5 : 0;
+    const float3 xs = make_float3(xs3[0], xs3[1], xs3[2]);
+    for (int c = gwarp; c < rch; c += nwarps) {  // warp-uniform
+        const int p = cb + c * 32 + lane;
+        const bool have = p >= pb && p < pe;
+        int r = -1;
+        FeatTerms ft = {};
+        if (have) {
+            int lo = 0, hi = SCHED_BATCH;  // largest t with boff[t] <= p
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (boff[mid] <= p) lo = mid;
+                else hi = mid;
+            }
+            r = r0 + lo;
+            const float4 l0 = __ldcg(a.elen + p), l1 = __ldcg(a.elen + a.n + p), x = __ldcg(a.pos + p);
+            const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+            float gb[PTP_TRI];
 #pragma unroll
-    for (int q = 0; q < FEAT_WORDS; ++q) acc[q] = 0ull;
+            for (int t = 0; t < PTP_TRI; ++t) gb[t] = __ldcg(a.tgeom + (size_t)t * a.n + p).x;
+            ft = feat_terms(__ldcg(a.meta + p), el, gb, make_float3(x.x, x.y, x.z), xs, a.feat_scale, a.feat_scale2);
+        }
+        bool todo = have;
+        while (__any_sync(0xffffffffu, todo)) {  // warp-uniform: one add per topleset present
+            const int lead = __ffs(__ballot_sync(0xffffffffu, todo)) - 1;
+            const int rl = __shfl_sync(0xffffffffu, r, lead);
+            const bool mine = todo && r == rl;
+            feat_warp_add(a.facc + (size_t)(rl % FEAT_RING) * FEAT_WORDS, ft, mine);
+            todo = todo && !mine;
+        }
+    }
 }
 
 // Topleset of band position p (two-step path, convergence traces only).
@@ -322,49 +366,33 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     // through iperm, geometry copied from the original mesh.  32-position
     // chunks are dealt to the warps from the last one down, so that in a
     // narrow band the copying warps are not the ones with band chunks.
-    // FUSED with the learned multi-advance band: the copy of topleset `lev`
-    // also adds its vertices' window-feature terms to the topleset's slot of
-    // the feature ring (ptp_schedule.cuh).
-    __shared__ float s_xs[3];  // the first source's position
-    auto copy_level = [&](int pb, int pe, int lev) {
+    auto copy_level = [&](int pb, int pe) {
         if constexpr (FUSED) {
             const int n = a.n;
             const int cb = pb & ~31;
             const int rch = pe > cb ? (pe - cb + 31) >> 5 : 0;
-            constexpr bool feats = MULTI;
-            for (int c = nwarps - 1 - gwarp; c < rch; c += nwarps) {  // warp-uniform
+            for (int c = nwarps - 1 - gwarp; c < rch; c += nwarps) {
                 const int p = cb + c * 32 + lane;
-                const bool have = p >= pb && p < pe;
-                FeatTerms ft = {};
-                if (have) {
-                    const int v = __ldcg(a.perm + p);
-                    const int4 s0 = __ldcg(a.ring_w + p), s1 = __ldcg(a.ring_w + n + p);
-                    float4 g[PTP_TRI];
+                if (p < pb || p >= pe) continue;
+                const int v = __ldcg(a.perm + p);
+                const int4 s0 = __ldcg(a.ring_w + p), s1 = __ldcg(a.ring_w + n + p);
+                float4 g[PTP_TRI];
 #pragma unroll
-                    for (int q = 0; q < PTP_TRI; ++q) g[q] = __ldg(a.otgeom + (size_t)q * n + v);
-                    const float4 e0 = __ldg(a.oelen + v), e1 = __ldg(a.oelen + n + v), x = __ldg(a.opos + v);
-                    const int vm = feats ? __ldcg(a.meta_w + p) : 0;
-                    auto mp = [&](int id) { return id >= 0 ? __ldcg(a.iperm + id) : -1; };
-                    a.ring_w[p] = make_int4(mp(s0.x), mp(s0.y), mp(s0.z), mp(s0.w));
-                    a.ring_w[n + p] = make_int4(mp(s1.x), mp(s1.y), mp(s1.z), mp(s1.w));
-                    a.pos_w[p] = x;
+                for (int q = 0; q < PTP_TRI; ++q) g[q] = __ldg(a.otgeom + (size_t)q * n + v);
+                const float4 e0 = __ldg(a.oelen + v), e1 = __ldg(a.oelen + n + v), x = __ldg(a.opos + v);
+                auto mp = [&](int id) { return id >= 0 ? __ldcg(a.iperm + id) : -1; };
+                a.ring_w[p] = make_int4(mp(s0.x), mp(s0.y), mp(s0.z), mp(s0.w));
+                a.ring_w[n + p] = make_int4(mp(s1.x), mp(s1.y), mp(s1.z), mp(s1.w));
+                a.pos_w[p] = x;
 #pragma unroll
-                    for (int q = 0; q < PTP_TRI; ++q) a.tgeom_w[(size_t)q * n + p] = g[q];
-                    a.elen_w[p] = e0;
-                    a.elen_w[n + p] = e1;
-                    if (feats) {
-                        const float el[PTP_RING] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-                        float gb[PTP_TRI];
-#pragma unroll
-                        for (int q = 0; q < PTP_TRI; ++q) gb[q] = g[q].x;
-                        ft = feat_terms(vm, el, gb, make_float3(x.x, x.y, x.z), make_float3(s_xs[0], s_xs[1], s_xs[2]),
-                                        a.feat_scale, a.feat_scale2);
-                    }
-                }
-                if (feats) feat_warp_add(a.facc + (size_t)(lev % FEAT_RING) * FEAT_WORDS, ft, have);
+                for (int q = 0; q < PTP_TRI; ++q) a.tgeom_w[(size_t)q * n + p] = g[q];
+                a.elen_w[p] = e0;
+                a.elen_w[n + p] = e1;
             }
         }
     };
+    __shared__ float s_xs[3];  // the first source's position
+    __shared__ int s_boff[SCHED_BATCH + 1];
     __shared__ __half s_mlp[(FUSED && MULTI) ? MLP_NPARAM_ : 1];
     if constexpr (FUSED && MULTI) {
         {
@@ -389,8 +417,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         }
         if constexpr (!PERM) {
             if (k == 1) {
-                copy_level(0, off_at(1), 0);  // V_0 and V_1
-                copy_level(off_at(1), off_at(2), 1);
+                copy_level(0, off_at(2));  // V_0 and V_1
                 if (ptp_grid_sync(a.ctrl->bar, 1, 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)ncta) < 0) {
                     status = PTP_ERR_TIMEOUT;
                     k = 0;
@@ -412,7 +439,19 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     // the toplesets V_{i+1} .. V_{gend-1} that are due (sched_due), band
     // positions [bd.vi_end, g_hi) with g_hi = off[gend].
     constexpr bool multi = MULTI;
-    int gend = 1, g_hi = 0;
+    // The group state is CTA-uniform: every thread computes the same values
+    // and writes them to shared memory (s_mg = gend, g_hi), where they cost the
+    // iteration no registers; the next write comes only after a CTA barrier
+    // that every reader of the previous values has passed.
+    __shared__ int s_mg[2];
+    if constexpr (MULTI) {
+        if (threadIdx.x == 0) {
+            s_mg[0] = 1;
+            s_mg[1] = 0;
+        }
+        __syncthreads();
+    }
+    __shared__ int s_pf[2][MULTI ? 9 : 1];
     const int slim = FUSED ? a.n + 8 : rho;  // entries of the schedule array
 
     for (; k >= 1 && k <= max_iter; ++k) {
@@ -422,9 +461,18 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                 break;
             }
             if constexpr (MULTI) {
-                // the schedule of the 32 toplesets whose features are now complete
-                if ((k % SCHED_BATCH) == SCHED_BATCH - 1 && gwarp == nwarps - 1)
-                    infer_batch(a, s_mlp, (int)k - (SCHED_BATCH - 1), rho);
+                // every SCHED_BATCH iterations: the feature sums of the last
+                // SCHED_BATCH toplesets copied, then (one iteration later, once
+                // the sums are complete) their schedule, one topleset per warp
+                if ((k % SCHED_BATCH) == SCHED_BATCH - 1) {
+                    const int r0 = (int)k - (SCHED_BATCH - 1);
+                    if (threadIdx.x <= SCHED_BATCH) s_boff[threadIdx.x] = off_at(r0 + (int)threadIdx.x);
+                    __syncthreads();
+                    feature_pass(a, r0, gwarp, nwarps, s_boff, s_xs);
+                }
+                if (k >= SCHED_BATCH && (k % SCHED_BATCH) == 0)
+                    for (int l = gwarp; l < SCHED_BATCH; l += nwarps)  // warp-uniform
+                        infer_one(a, s_mlp, (int)k - SCHED_BATCH + l, rho);
             }
         }
         const int j = k < rho ? (int)k : rho - 1;
@@ -436,6 +484,16 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         const int first = bd.lo > nsrc ? bd.lo : nsrc;
         const int start = bd.copy_lo < first ? bd.copy_lo : first;
         const bool testing = multi || k >= check_from;
+        // multi: what the next group end needs (schedule and offsets from gend
+        // on), one value per thread 0..8, loaded now and put in shared memory
+        // at the end of the iteration
+        int *const pf = s_pf[k & 1];
+        int pfv = 0x3fffffff;
+        if constexpr (multi) {
+            const int q = threadIdx.x, ge = s_mg[0];
+            if (q < 4) pfv = ge + q < slim ? __ldcg(a.sched + ge + q) : 0x3fffffff;
+            else if (q < 9) pfv = off_at(ge + q - 4 < a.n + 1 ? ge + q - 4 : a.n + 1);
+        }
 
         int notconv = 0, gnotconv = 0, n_active = 0, n_changed = 0;
         float maxrel = 0.0f;
@@ -446,8 +504,8 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         // Recompute band vertex u from d_{k-1}, given its one-ring slots and
         // geometry: write d_k (and its label), stamp the neighbours if it
         // changed, and apply the relative-change test to V_{i_{k-1}}.
-        auto recompute = [&](int u, bool in_vi, bool in_g, float dold, int meta, int4 r0, int4 r1, float4 l0,
-                             float4 l1, const float4 *g) {
+        auto recompute = [&](int u, bool in_vi, float dold, int meta, int4 r0, int4 r1, float4 l0, float4 l1,
+                             const float4 *g) {
             const int ids[PTP_RING] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
             const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
             const int m = meta & PTP_META_CNT;
@@ -468,6 +526,9 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                     for (int t = 0; t < PTP_RING; ++t)
                         if (t < m) a.nstamp[ids[t]] = (int)k;
                 }
+                // multi: the group's test, for its vertices (u is the band
+                // position here; the group is [bd.vi_end, s_mg[1]))
+                const bool in_g = multi && u >= bd.vi_end && u < s_mg[1];
                 if ((in_vi && testing) || in_g || a.conv_trace) {
                     // relative-change test of Eq. lower_band, in FP64 (the
                     // difference of two floats is exact in double)
@@ -531,7 +592,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                     dnx[u] = dold;
                     if (LABELS) lnx[u] = __ldcg(lp + u);
                 }
-                if (need) recompute(u, p < bd.vi_end, multi && p >= bd.vi_end && p < g_hi, dold, meta, r0, r1, l0, l1, g);
+                if (need) recompute(u, p < bd.vi_end, dold, meta, r0, r1, l0, l1, g);
             }
         } else {
             // chunks of this CTA's warps: c = gwarp + m * nwarps, m = 0, 1, ...
@@ -579,9 +640,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                             at = __shfl_sync(0xffffffffu, at, 0);
                             if (need)
                                 s_queue[at + __popc(bal & ((1u << lane) - 1u))] =
-                                    make_int2(uu[q] | (pp[q] < bd.vi_end ? (int)0x80000000 : 0) |
-                                                  (multi && pp[q] >= bd.vi_end && pp[q] < g_hi ? 0x40000000 : 0),
-                                              __float_as_int(dold[q]));
+                                    make_int2(uu[q] | (pp[q] < bd.vi_end ? (int)0x80000000 : 0), __float_as_int(dold[q]));
                         }
                     }
                 }
@@ -590,13 +649,12 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                 const int nq = s_nq;
                 for (int q = threadIdx.x; q < nq; q += blockDim.x) {
                     const int2 ent = s_queue[q];
-                    const int u = ent.x & 0x3fffffff;
+                    const int u = ent.x & 0x7fffffff;
                     int meta;
                     int4 r0, r1;
                     float4 l0, l1, g[PTP_TRI];
                     load_slots(u, meta, r0, r1, l0, l1, g);
-                    recompute(u, ent.x < 0, multi && (ent.x & 0x40000000) != 0, __int_as_float(ent.y), meta, r0, r1, l0,
-                              l1, g);
+                    recompute(u, ent.x < 0, __int_as_float(ent.y), meta, r0, r1, l0, l1, g);
                 }
                 // the queue is refilled by the next round; after the last one
                 // only in the next iteration, behind the grid barrier, so warps
@@ -607,7 +665,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         // V_{k+1} into topleset order for the next iteration, by the warps
         // counted from the last one down: in a narrow band not the band's
         // warps, in a wide one the warps with the fewest queued vertices
-        if constexpr (FUSED && !PERM) copy_level(off_at((int)k + 1), off_at((int)k + 2), (int)k + 1);
+        if constexpr (FUSED && !PERM) copy_level(off_at((int)k + 1), off_at((int)k + 2));
         tot_active += n_active;
         tot_changed += n_changed;
 
@@ -645,13 +703,11 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         const int o_i2 = off_at(i + 2);
         const int o_jn = off_at(jn), o_jn1 = off_at(jn + 1);
         const int sched_next = (a.sched && !multi && i + 1 < rho) ? __ldcg(a.sched + i + 1) : 1;
-        // multi: what the next group end needs (schedule and offsets from gend on)
-        int pf_s[4], pf_o[5];
+        // multi: every thread reads the prefetched values after the grid
+        // barrier, whose last step is a CTA barrier (two buffers by iteration
+        // parity, so the next write waits a barrier)
         if constexpr (multi) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) pf_s[q] = gend + q < slim ? __ldcg(a.sched + gend + q) : 0x3fffffff;
-#pragma unroll
-            for (int q = 0; q < 5; ++q) pf_o[q] = off_at(gend + q < a.n + 1 ? gend + q : a.n + 1);
+            if (threadIdx.x < 9) pf[threadIdx.x] = pfv;
         }
 
         const int any = __syncthreads_or(notconv);
@@ -668,6 +724,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         const bool bottom_ok = (failed & 0xffff) == 0, group_ok = (failed >> 16) == 0;
         const bool advance = a.band_mode == 1 ? (int)((k + 1) >> 1) > i : (testing && bottom_ok);
         // multi: the bottom and every due topleset above it passed: retire them all
+        const int gend = multi ? s_mg[0] : 1;
         const bool jump = multi && advance && gend > i + 1 && group_ok;
         if (leader) {
             band_updates += bd.hi - first;
@@ -688,8 +745,8 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                 status = PTP_OK;
                 break;
             }
-            bd.lo = pf_o[0];
-            bd.vi_end = pf_o[1];
+            bd.lo = pf[4];
+            bd.vi_end = pf[5];
         } else if (advance) {
             // i_k = i_{k-1} + 1: V_{i_{k-1}} retires and is copied forward in
             // the next iteration (V_0 never changes)
@@ -711,9 +768,11 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             // the next group: from V_{i+1} on, every topleset due by iteration
             // k + 1 (at most four more per iteration, from the prefetch)
             int g = gend > i + 1 ? gend : i + 1;
-            while (g - gend < 4 && g < rho && sched_due(g, pf_s[g - gend]) <= k + 1) ++g;
-            g_hi = pf_o[g - gend];
-            gend = g;
+            while (g - gend < 4 && g < rho && sched_due(g, pf[g - gend]) <= k + 1) ++g;
+            const int ghi = pf[4 + g - gend];
+            __syncwarp();
+            s_mg[0] = g;  // the same values from every thread
+            s_mg[1] = ghi;
         }
         bd.vj_beg = o_jn;
         bd.hi = o_jn1;

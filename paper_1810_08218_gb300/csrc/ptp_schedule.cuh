@@ -43,10 +43,12 @@ static_assert(FEAT_RING * FEAT_WORDS == PTP_FEAT_RING_WORDS, "feature ring size"
 // Iteration from which topleset r, entering the band at iteration r, may
 // join the tested group of the learned multi-advance band: its predicted
 // delay after entry, but not before its schedule is visible to every CTA of
-// a fused launch (inferred with its batch of SCHED_BATCH at the iteration
-// after the batch's last topleset was copied, read one iteration ahead).
+// a fused launch.  There the toplesets of a batch b (r / SCHED_BATCH = b)
+// have their features summed at iteration 32 b + 31 (the last one copied at
+// 32 b + 30), their schedule inferred at 32 b + 32, and it is read one
+// iteration ahead, so it serves from iteration 32 b + 34 on.
 __host__ __device__ __forceinline__ long long sched_due(int r, int sched) {
-    const long long vis = (long long)SCHED_BATCH * (r / SCHED_BATCH) + SCHED_BATCH + 1;
+    const long long vis = (long long)SCHED_BATCH * (r / SCHED_BATCH) + SCHED_BATCH + 2;
     const long long pred = (long long)r + (sched > 1 ? sched : 1);
     return pred > vis ? pred : vis;
 }
@@ -56,19 +58,20 @@ __device__ __forceinline__ long long fixq(double v, double scale) { return llrin
 // One vertex's contribution to its topleset's sums: ring-edge lengths and
 // their squares, the distance to the first source and its square (fixed
 // point, scales 2^30 / diameter and 2^30 / diameter^2), the ring-edge count
-// and the smallest angle at the vertex between consecutive ring neighbours.
+// and the largest cosine of an angle at the vertex between consecutive ring
+// neighbours (the smallest angle is its arc cosine, taken once per topleset).
 // el: the ring-edge lengths, gb: the dot products e_t . e_{t+1} of the ring
 // triangles (the first component of the ring geometry).
 struct FeatTerms {
     long long se, se2, sr, sr2;
     int edges;
-    float amin;
+    float cmax;  // largest cosine of an angle at the vertex (-1: none)
 };
 
 __device__ __forceinline__ FeatTerms feat_terms(int meta, const float el[PTP_RING], const float gb[PTP_TRI], float3 x,
                                                 float3 xs, double scale, double scale2) {
     const int cnt = (meta & PTP_META_GENERAL) ? 0 : (meta & PTP_META_CNT);
-    float es = 0.0f, eq = 0.0f, amin = 3.14159265f;
+    float es = 0.0f, eq = 0.0f, cmax = -1.0f;  // the smallest angle has the largest cosine
 #pragma unroll
     for (int t = 0; t < PTP_RING; ++t) {
         if (t < cnt) {
@@ -80,7 +83,7 @@ __device__ __forceinline__ FeatTerms feat_terms(int meta, const float el[PTP_RIN
     for (int t = 0; t < PTP_TRI; ++t) {
         if (t < cnt - 1) {
             const float den = el[t] * el[t + 1];
-            if (den > 0.0f) amin = fminf(amin, acosf(fmaxf(-1.0f, fminf(1.0f, gb[t] / den))));
+            if (den > 0.0f) cmax = fmaxf(cmax, fmaxf(-1.0f, fminf(1.0f, gb[t] / den)));
         }
     }
     const float dx = x.x - xs.x, dy = x.y - xs.y, dz = x.z - xs.z;
@@ -92,7 +95,7 @@ __device__ __forceinline__ FeatTerms feat_terms(int meta, const float el[PTP_RIN
     f.sr = fixq((double)rad, scale);
     f.sr2 = fixq((double)r2, scale2);
     f.edges = cnt;
-    f.amin = amin;
+    f.cmax = cmax;
     return f;
 }
 
@@ -101,7 +104,7 @@ __device__ __forceinline__ FeatTerms feat_terms(int meta, const float el[PTP_RIN
 __device__ __forceinline__ void feat_warp_add(unsigned long long *acc, const FeatTerms &f, bool have) {
     long long se = have ? f.se : 0, se2 = have ? f.se2 : 0, sr = have ? f.sr : 0, sr2 = have ? f.sr2 : 0;
     int ed = have ? f.edges : 0, cnt = have ? 1 : 0;
-    float am = have ? f.amin : 3.14159265f;
+    float cm = have ? f.cmax : -1.0f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         se += __shfl_xor_sync(0xffffffffu, se, o);
@@ -110,7 +113,7 @@ __device__ __forceinline__ void feat_warp_add(unsigned long long *acc, const Fea
         sr2 += __shfl_xor_sync(0xffffffffu, sr2, o);
         ed += __shfl_xor_sync(0xffffffffu, ed, o);
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        am = fminf(am, __shfl_xor_sync(0xffffffffu, am, o));
+        cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
     }
     if ((threadIdx.x & 31) == 0 && cnt > 0) {
         atomicAdd(acc + 0, (unsigned long long)se);
@@ -119,9 +122,9 @@ __device__ __forceinline__ void feat_warp_add(unsigned long long *acc, const Fea
         atomicAdd(acc + 3, (unsigned long long)sr2);
         atomicAdd(acc + 4, (unsigned long long)ed);
         atomicAdd(acc + 5, (unsigned long long)cnt);
-        // angles in [0, pi] order like their bit patterns, so the largest
-        // bits(pi) - bits(angle) is the smallest angle (0 in a fresh slot = pi)
-        atomicMax(acc + 6, (unsigned long long)(__float_as_uint(3.14159265f) - __float_as_uint(am)));
+        // 1 + cos lies in [0, 2], where floats order like their bit patterns
+        // (a fresh slot, 0, reads as cos = -1)
+        atomicMax(acc + 6, (unsigned long long)__float_as_uint(1.0f + cm));
     }
 }
 
@@ -132,7 +135,7 @@ __device__ __forceinline__ void feat_finalize(const unsigned long long *acc, int
     const double se = (double)(long long)acc[0], se2 = (double)(long long)acc[1];
     const double sr = (double)(long long)acc[2], sr2 = (double)(long long)acc[3];
     const double ed = (double)acc[4], c = (double)acc[5];
-    const float amin = __uint_as_float(__float_as_uint(3.14159265f) - (unsigned)acc[6]);
+    const float amin = acosf(fmaxf(-1.0f, fminf(1.0f, __uint_as_float((unsigned)acc[6]) - 1.0f)));
     double cv_e = 0.0, cv_r = 0.0;
     if (ed > 0.0 && se > 0.0) {
         // both sums are scaled by 2^30 / diameter (squares by its square), so
@@ -173,6 +176,26 @@ __device__ __forceinline__ float mlp_forward(const __half *w, const float x[MLP_
     float y = __half2float(w[MLP_OB3]);
 #pragma unroll
     for (int i = 0; i < MLP_H; ++i) y = fmaf(__half2float(w[MLP_OW3 + i]), h2[i], y);
+    return y;
+}
+
+// The same forward pass as mlp_forward for one sample, spread over a warp
+// (lane j computes hidden unit j of both layers in the same order; the output
+// sums the units in order, as mlp_forward does), with no per-thread arrays.
+// Every lane returns y.  x must be the same on every lane.
+__device__ __forceinline__ float mlp_forward_warp(const __half *w, const float x[MLP_NIN]) {
+    const int j = threadIdx.x & 31;
+    float z = __half2float(w[MLP_OB1 + j]);
+#pragma unroll
+    for (int i = 0; i < MLP_NIN; ++i) z = fmaf(__half2float(w[MLP_OW1 + j * MLP_NIN + i]), x[i], z);
+    const float h1 = fmaxf(z, 0.0f);
+    z = __half2float(w[MLP_OB2 + j]);
+#pragma unroll
+    for (int i = 0; i < MLP_H; ++i) z = fmaf(__half2float(w[MLP_OW2 + j * MLP_H + i]), __shfl_sync(0xffffffffu, h1, i), z);
+    const float h2 = fmaxf(z, 0.0f);
+    float y = __half2float(w[MLP_OB3]);
+#pragma unroll
+    for (int i = 0; i < MLP_H; ++i) y = fmaf(__half2float(w[MLP_OW3 + i]), __shfl_sync(0xffffffffu, h2, i), y);
     return y;
 }
 
