@@ -85,10 +85,14 @@ SINGLE_STEP = ("ptp_mesh_create + ptp_distance_from_sources (corner lists and sl
                "renumbering and the window iteration in one launch: all hot-path stages)")
 
 
-def _config(workload: str, world: int) -> dict:
+TWO_STEP = ("ptp_mesh_create + ptp_toplesets (cluster BFS, renumbering) + ptp_distance (the window iteration "
+            "in its own launch)")
+
+
+def _config(workload: str, world: int, path: str = "fused") -> dict:
     return {"workload": WORKLOADS[workload], "l2": "flushed between steps (256 MiB write)",
             "parallelism": f"independent replicas x{world}" if world > 1 else "single GPU",
-            "step": STEPS.get(workload, SINGLE_STEP)}
+            "step": STEPS.get(workload, TWO_STEP if path == "two_step" else SINGLE_STEP)}
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -305,6 +309,26 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+LEARNED_WORKLOADS = ("torus_1m", "sphere_l7")
+
+
+def learned_vs_plain(V, F, S) -> dict:
+    """The learned multi-advance band against the plain band, both in
+    fixpoint mode (eps = 1e-7) through the fused launch on the resident
+    mesh: median ms per map of 10 runs (CUDA events), K, band updates and
+    max |d_learned - d_plain| / diameter."""
+    from paper_1810_08218_gb300 import learned
+
+    w, meta = learned.load_weights()
+    r = learned.compare(V, F, S, w, meta["margin"], eps=learned.FIXPOINT_EPS, reps=10, warm=3)
+    out = {"eps": learned.FIXPOINT_EPS, "margin": meta["margin"], "unit": "ms per map"}
+    for k in ("plain", "learned"):
+        out[k] = {"ms": round(r[k]["ms"], 4), "K": r[k]["K"], "band_updates": r[k]["band_updates"]}
+    out["learned_over_plain_ms"] = round(r["learned"]["ms"] / r["plain"]["ms"], 4)
+    out["max_abs_dd_over_diam"] = r["max_abs_dd_over_diam"]
+    return out
+
+
 def map_accuracy(workload: str, d_gpu: np.ndarray, V32: np.ndarray, S, d_oracle) -> dict:
     """max |d_gpu - d_oracle| / diameter against the oracle's map at the same
     eps, and the mean relative error against the exact distance where the
@@ -378,8 +402,14 @@ def run_ours(args) -> None:
             params.ev_begin = None
             params.ev_end = None
         mesh = capi.ptp_mesh_create(Vt, Ft)
-        # toplesets (BFS, renumbering) and the iteration in one launch
-        capi.ptp_distance_from_sources(mesh, S_host, params, d, stats=False)
+        if args.path == "two_step":
+            # toplesets (cluster BFS, renumbering), then the window launch
+            tops = capi.ptp_toplesets(mesh, S_host)
+            capi.ptp_distance(tops, params, d, stats=False)
+            capi.ptp_toplesets_destroy(tops)
+        else:
+            # toplesets (BFS, renumbering) and the iteration in one launch
+            capi.ptp_distance_from_sources(mesh, S_host, params, d, stats=False)
         return mesh
 
     for _ in range(args.warmup):
@@ -419,7 +449,12 @@ def run_ours(args) -> None:
     mesh = capi.ptp_mesh_create(Vt, Ft)
     params.ev_begin = None
     params.ev_end = None
-    stats = capi.ptp_distance_from_sources(mesh, S_host, params, d, stats=True)
+    if args.path == "two_step":
+        tops = capi.ptp_toplesets(mesh, S_host)
+        stats = capi.ptp_distance(tops, params, d, stats=True)
+        capi.ptp_toplesets_destroy(tops)
+    else:
+        stats = capi.ptp_distance_from_sources(mesh, S_host, params, d, stats=True)
     capi.ptp_mesh_destroy(mesh)
     d_map = d.cpu().numpy()
     total_ms = max_over_ranks(float(sum(step_ms)), dev)
@@ -453,9 +488,10 @@ def run_ours(args) -> None:
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": _config(args.workload, world),
+            "config": _config(args.workload, world, args.path),
             "window_kernel_ms": round(kavg, 4),
-            "timed_kernel": "ptp_window, fused: BFS toplesets, renumbering and the iteration in one launch",
+            "timed_kernel": ("ptp_window, fused: BFS toplesets, renumbering and the iteration in one launch"
+                             if args.path == "fused" else "ptp_window, the iteration alone (toplesets built before)"),
             "vertex_updates_per_s": round(stats["band_updates"] / (kavg * 1e-3), 1),
             "ptp": {"K": stats["iterations"], "rho": stats["rho"], "band_updates": stats["band_updates"],
                     "active_updates": stats["active_updates"], "fp64_solves": stats["fp64_solves"]},
@@ -469,6 +505,8 @@ def run_ours(args) -> None:
             "clocks": clocks,
             "wall_s": round(wall, 3),
         }
+        if args.workload in LEARNED_WORKLOADS:
+            line["learned_schedule"] = learned_vs_plain(V, F, S)
         d_oracle = None
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"], d_oracle = cpu_oracle_full_map(args.workload, V, F, S)
@@ -708,6 +746,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="torus_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--path", choices=["fused", "two_step"], default="fused",
+                    help="single-map workloads: the fused launch (default) or ptp_toplesets + ptp_distance")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
