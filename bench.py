@@ -132,7 +132,7 @@ def _kernel_source_hash() -> str:
     import re
 
     h = hashlib.sha256()
-    for f in ("ptp_distance.cu", "ptp_update.cuh", "ptp_internal.cuh"):
+    for f in ("ptp_distance.cu", "ptp_update.cuh", "ptp_internal.cuh", "ptp_schedule.cuh"):
         with open(os.path.join(ROOT, "paper_1810_08218_gb300", "csrc", f)) as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
