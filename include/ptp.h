@@ -107,8 +107,8 @@ typedef struct ptp_params {
     const void *mlp_half;   /* band_mode 2 in ptp_distance_from_sources: DEVICE
                           array of PTP_MLP_NPARAM FP16 weights of the schedule
                           MLP.  The launch computes each topleset's window
-                          features while it copies it into topleset order and
-                          infers its schedule inside the launch, with the same
+                          features once it is in topleset order and infers
+                          its schedule inside the launch, with the same
                           arithmetic as ptp_window_features + ptp_mlp_infer, so
                           the two paths run the same iteration                  */
     float mlp_margin;       /* margin of that inference (see ptp_mlp_infer)       */

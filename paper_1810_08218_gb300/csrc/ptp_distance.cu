@@ -168,6 +168,112 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a, int *stage_smem) {
     }
 }
 
+// Band position p of a topleset-ordered fused launch into place: the
+// producers' record there (meta, raw slots as original ids) gets its slots
+// remapped through iperm and the vertex's geometry copied from the original
+// mesh.  Every slot's vertex must have its position (iperm) by then.
+__device__ __forceinline__ void copy_position(const DistArgs &a, int p) {
+    const int n = a.n;
+    const int v = __ldcg(a.perm + p);
+    const int4 s0 = __ldcg(a.ring_w + p), s1 = __ldcg(a.ring_w + n + p);
+    float4 g[PTP_TRI];
+#pragma unroll
+    for (int q = 0; q < PTP_TRI; ++q) g[q] = __ldg(a.otgeom + (size_t)q * n + v);
+    const float4 e0 = __ldg(a.oelen + v), e1 = __ldg(a.oelen + n + v), x = __ldg(a.opos + v);
+    auto mp = [&](int id) { return id >= 0 ? __ldcg(a.iperm + id) : -1; };
+    a.ring_w[p] = make_int4(mp(s0.x), mp(s0.y), mp(s0.z), mp(s0.w));
+    a.ring_w[n + p] = make_int4(mp(s1.x), mp(s1.y), mp(s1.z), mp(s1.w));
+    a.pos_w[p] = x;
+#pragma unroll
+    for (int q = 0; q < PTP_TRI; ++q) a.tgeom_w[(size_t)q * n + p] = g[q];
+    a.elen_w[p] = e0;
+    a.elen_w[n + p] = e1;
+}
+
+// Copy CTAs of a topleset-ordered fused launch: the a.copiers CTAs before
+// the producers put the toplesets into place as the BFS publishes them, so
+// that the window CTAs spend no iteration time on it.  Topleset V_r can be
+// copied once every vertex of its one-ring has a position, that is once
+// V_{r+1} is complete (ctrl->ready >= r + 2).  A round copies V_done ..
+// V_{upto-1}: every copy CTA waits (thread 0, acquire) until ctrl->ready
+// >= upto + 1, the positions are dealt to the copy threads in 32-position
+// chunks (warps interleaved across the copy CTAs, so a small topleset still
+// spreads over all of them), the copy CTAs pass their own grid barrier and
+// one thread publishes ctrl->copied = upto with a release store.  Every copy
+// CTA must copy the same range (each position exactly once: a second copy
+// would remap slots that are already positions), so the next range comes
+// from the barrier: copy CTA 0 adds how far the latest ctrl->ready it saw
+// is past upto + 1 (or a flag once the BFS has ended) and the others 0, and
+// the sum, the same in every CTA, sets the next upto (every topleset
+// copyable by then, at least one more).  When the BFS is ahead, a round
+// takes many toplesets.  Once ctrl->ready is PTP_LEVELS_DONE the next
+// round ends at rho, which every copy CTA reads after its own wait, and
+// ctrl->copied becomes PTP_LEVELS_DONE.  The window CTAs acquire
+// ctrl->copied before they read the copied toplesets and the offsets;
+// ctrl->copied >= r + 1 implies ctrl->ready >= r + 2, so off[0 .. r+2] are
+// published as well.  Copy CTAs never wait for the window CTAs.
+__device__ __noinline__ void level_copier(const DistArgs &a) {
+    const int C = a.copiers;
+    const int cid = (int)blockIdx.x - ((int)gridDim.x - a.producers - C);
+    const int lane = threadIdx.x & 31;
+    const int cwarp = (int)(threadIdx.x >> 5) * C + cid;  // warps interleaved across the copy CTAs
+    const int ncw = (int)(blockDim.x >> 5) * C;
+    constexpr int TO_RHO = 0x7fffffff;  // the round ends at rho (the BFS has ended)
+    __shared__ int s_now[2];
+    unsigned long long prev_hi[2] = {0ull, 0ull};
+    int done = 0, upto = 1;  // the first round copies V_0
+    for (long long e = 1;; ++e) {
+        if (threadIdx.x == 0) {
+            int now = 0, ok = 1;
+            const long long t0 = clock64();
+            unsigned spins = 0;
+            while (true) {
+                now = ptp_ld_acquire_s32(&a.ctrl->ready);
+                if (now >= (upto == TO_RHO ? PTP_LEVELS_DONE : upto + 1)) break;
+                if ((++spins & 63u) == 0) {
+                    if (*(volatile int *)&a.ctrl->abort) { ok = 0; break; }
+                    if (clock64() - t0 > PTP_WAIT_CYCLES) {
+                        atomicExch(&a.ctrl->status, (int)PTP_ERR_TIMEOUT);
+                        atomicExch(&a.ctrl->abort, 1);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+            s_now[0] = ok;
+            s_now[1] = (ok && now == PTP_LEVELS_DONE) ? __ldcg(a.info) : TO_RHO;  // rho once known
+        }
+        __syncthreads();
+        if (!s_now[0]) return;
+        if (upto == TO_RHO) upto = s_now[1];  // every copy CTA has seen the BFS end
+        const int pb = __ldcg(a.off + done), pe = __ldcg(a.off + upto);
+        const int cb = pb & ~31;
+        const int rch = pe > cb ? (pe - cb + 31) >> 5 : 0;
+        for (int c = cwarp; c < rch; c += ncw) {
+            const int p = cb + c * 32 + lane;
+            if (p >= pb && p < pe) copy_position(a, p);
+        }
+        // the BFS's progress for the next range, from copy CTA 0 only: how
+        // many toplesets past upto are copyable, or BFS_ENDED (the barrier
+        // sums the values of all its epochs in 32 bits, so they stay small)
+        constexpr unsigned BFS_ENDED = 1u << 30;
+        unsigned seen = 0;
+        if (cid == 0 && threadIdx.x == 0) {
+            const int rd = ptp_ld_acquire_s32(&a.ctrl->ready);  // >= upto + 1, seen above
+            seen = rd == PTP_LEVELS_DONE ? BFS_ENDED : (unsigned)min(rd - (upto + 1), 1 << 20);
+        }
+        // s_now is rewritten only after this barrier's last CTA barrier
+        const long long sum = ptp_grid_sync(a.ctrl->cbar, e, seen, &a.ctrl->abort, &a.ctrl->status, prev_hi,
+                                            (unsigned)C);
+        if (sum < 0) return;
+        const bool last = upto == s_now[1];  // V_{rho-1} is in place
+        if (cid == 0 && threadIdx.x == 0) ptp_st_release_s32(&a.ctrl->copied, last ? PTP_LEVELS_DONE : upto);
+        if (last) return;
+        done = upto;
+        upto = sum >= BFS_ENDED ? TO_RHO : done + (sum > 0 ? (int)sum : 1);
+    }
+}
+
 // Learned multi-advance band in a fused launch: the schedule of topleset r
 // (one warp), from the feature sums its copy accumulated (ptp_schedule.cuh)
 // and the MLP whose FP16 weights are in `w`; the sums' ring slot is cleared
@@ -193,7 +299,7 @@ __device__ __noinline__ void infer_one(const DistArgs &a, const __half *w, int r
 }
 
 // Learned multi-advance band in a fused launch: the window-feature sums of
-// toplesets r0 .. r0 + 31 (copied into topleset order in earlier iterations;
+// toplesets r0 .. r0 + 31 (already in topleset order;
 // boff[t] = off[r0 + t]) into their slots of the feature ring, by every warp
 // of the window CTAs at once.  Kept out of line: it runs once every
 // SCHED_BATCH iterations and must not add to the iteration's registers.
@@ -262,16 +368,17 @@ __device__ __forceinline__ int topleset_of(const int *__restrict__ off, int rho,
 // renumbered mesh.  LABELS: also carry a label per vertex (Voronoi regions).
 //
 // FUSED (ptp_distance_from_sources): the toplesets are built inside this
-// launch.  The last a.producers CTAs run the BFS (bfs_producer); the others
-// run the iteration on a topleset-ordered copy of the mesh: the producers
-// write each vertex's meta and raw slots at its position when they claim
-// it, and the window CTAs complete V_{k+1} during iteration k (copy_level)
-// with the slots remapped through iperm and the geometry copied from the
-// original mesh.  Before iteration k a window
-// CTA waits until off[0 .. k+3] are published (V_{k+2}'s positions are then
-// known, which the copy of V_{k+1} needs).  rho is unknown until the BFS
-// ends; until then every window CTA has seen at least k+3 published levels,
-// so rho > k+2 and j_k = k, the same decision the known rho would give.
+// launch.  The last a.producers CTAs run the BFS (bfs_producer).  In
+// topleset order the a.copiers CTAs before them put each topleset into
+// place (level_copier): the producers write each vertex's meta and raw
+// slots at its position when they claim it, the copiers remap the slots
+// through iperm and copy the geometry from the original mesh.  The other
+// CTAs run the iteration.  Before iteration k a window CTA waits until
+// V_0 .. V_k are copied (ctrl->copied >= k + 1, which implies that off[0 ..
+// k+2] are published); in the original order, until off[0 .. k+3] are
+// published (ctrl->ready >= k + 3).  rho is unknown until the BFS ends;
+// until then V_{k+1} is known to be non-empty, so rho > k + 1 and j_k = k,
+// the same decision the known rho would give.
 template <bool PERM, bool LABELS, bool FUSED = false, bool MULTI = false>
 __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(DistArgs a) {
     static_assert(!(MULTI && PERM), "the learned multi-advance band runs in topleset order");
@@ -284,9 +391,15 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             bfs_producer(a, reinterpret_cast<int *>(s_queue));
             return;
         }
+        if constexpr (!PERM) {
+            if ((int)blockIdx.x >= (int)gridDim.x - a.producers - a.copiers) {
+                level_copier(a);
+                return;
+            }
+        }
     }
     constexpr int RHO_UNKNOWN = 0x3fffffff;
-    const int ncta = FUSED ? (int)gridDim.x - a.producers : (int)gridDim.x;  // window CTAs
+    const int ncta = FUSED ? (int)gridDim.x - a.producers - (PERM ? 0 : a.copiers) : (int)gridDim.x;  // window CTAs
     int rho = FUSED ? RHO_UNKNOWN : __ldcg(a.info);
     const int nsrc = __ldcg(a.off + 1);
     long long max_iter = a.max_iter > 0 ? a.max_iter : (FUSED ? (1LL << 40) : 8LL * rho + 64);
@@ -311,19 +424,22 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     auto off_at = [&](int r) { return __ldcg(a.off + (r < rho ? r : rho)); };
     // the queue is written during a fused launch: read it through L2 there
     auto vertex_at = [&](int pos) { return PERM ? (FUSED ? __ldcg(a.perm + pos) : __ldg(a.perm + pos)) : pos; };
-    // FUSED: wait until off[0 .. need] are published (or the BFS has ended);
-    // afterwards rho is set if known.  Called by every thread of the CTA.
+    // FUSED: wait until the progress word (ctrl->copied in topleset order,
+    // ctrl->ready in the original order) reaches `need` (or the BFS has
+    // ended); afterwards rho is set if known.  Called by every thread of the
+    // CTA.
     // Returns false when a wait timed out or another CTA aborted.
     // Every thread keeps the progress its CTA has seen (`seen`, updated by
     // all threads from the same shared value after the barrier below, so it
     // is uniform), and when the BFS is already far enough ahead (the common
-    // case) the CTA passes no barrier here; ctrl->ready is polled, by thread
-    // 0, only when it is not.  rho becomes known at the first poll after the
+    // case) the CTA passes no barrier here; the word is polled, by thread 0,
+    // only when it is not.  rho becomes known at the first poll after the
     // BFS has ended, in every CTA before it needs it (need > rho by then).
     // Consecutive calls are separated by a CTA barrier (the grid barrier),
     // which keeps s_wait from being rewritten before every thread read it.
     __shared__ int s_wait[3];
-    int seen = 1;  // off[0], off[1] are set before launch
+    int *const progress = PERM ? &a.ctrl->ready : &a.ctrl->copied;
+    int seen = PERM ? 1 : 0;  // off[0], off[1] are set before launch
     auto wait_levels = [&](int need) -> bool {
         if (seen >= need) return true;
         if (threadIdx.x == 0) {
@@ -332,7 +448,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             const long long t0 = clock64();
             unsigned spins = 0;
             while (true) {
-                now = ptp_ld_acquire_s32(&a.ctrl->ready);
+                now = ptp_ld_acquire_s32(progress);
                 if (now >= need) break;
                 if ((++spins & 63u) == 0) {
                     if (*(volatile int *)&a.ctrl->abort) { ok = 0; break; }
@@ -357,40 +473,9 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         }
         return ok;
     };
-    // what iteration k needs from the producers: offsets up to off[k+2]; in
-    // topleset order also the positions of V_{k+2}, since iteration k copies
-    // V_{k+1} (whose slots point into V_{k+2}) for iteration k+1
-    auto need_for = [](long long kk) { return (int)kk + 3; };
-    // FUSED in topleset order: complete the vertices at positions [pb, pe)
-    // (their meta and raw slots are the producers' records): slots remapped
-    // through iperm, geometry copied from the original mesh.  32-position
-    // chunks are dealt to the warps from the last one down, so that in a
-    // narrow band the copying warps are not the ones with band chunks.
-    auto copy_level = [&](int pb, int pe) {
-        if constexpr (FUSED) {
-            const int n = a.n;
-            const int cb = pb & ~31;
-            const int rch = pe > cb ? (pe - cb + 31) >> 5 : 0;
-            for (int c = nwarps - 1 - gwarp; c < rch; c += nwarps) {
-                const int p = cb + c * 32 + lane;
-                if (p < pb || p >= pe) continue;
-                const int v = __ldcg(a.perm + p);
-                const int4 s0 = __ldcg(a.ring_w + p), s1 = __ldcg(a.ring_w + n + p);
-                float4 g[PTP_TRI];
-#pragma unroll
-                for (int q = 0; q < PTP_TRI; ++q) g[q] = __ldg(a.otgeom + (size_t)q * n + v);
-                const float4 e0 = __ldg(a.oelen + v), e1 = __ldg(a.oelen + n + v), x = __ldg(a.opos + v);
-                auto mp = [&](int id) { return id >= 0 ? __ldcg(a.iperm + id) : -1; };
-                a.ring_w[p] = make_int4(mp(s0.x), mp(s0.y), mp(s0.z), mp(s0.w));
-                a.ring_w[n + p] = make_int4(mp(s1.x), mp(s1.y), mp(s1.z), mp(s1.w));
-                a.pos_w[p] = x;
-#pragma unroll
-                for (int q = 0; q < PTP_TRI; ++q) a.tgeom_w[(size_t)q * n + p] = g[q];
-                a.elen_w[p] = e0;
-                a.elen_w[n + p] = e1;
-            }
-        }
-    };
+    // what iteration k needs: V_0 .. V_k in place (topleset order), or the
+    // offsets off[0 .. k+3] (original order)
+    auto need_for = [](long long kk) { return (int)kk + (PERM ? 3 : 1); };
     __shared__ float s_xs[3];  // the first source's position
     __shared__ int s_boff[SCHED_BATCH + 1];
     __shared__ __half s_mlp[(FUSED && MULTI) ? MLP_NPARAM_ : 1];
@@ -407,22 +492,10 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             __syncthreads();
         }
     }
-    // barrier epochs: the topleset-ordered fused run has one more barrier,
-    // after copying V_0 and V_1, so its iteration k uses epoch k + 1
-    constexpr long long EP0 = (FUSED && !PERM) ? 1 : 0;
     if constexpr (FUSED) {
         if (!wait_levels(need_for(1))) {
             status = PTP_ERR_TIMEOUT;
             k = 0;  // the loop below does not run
-        }
-        if constexpr (!PERM) {
-            if (k == 1) {
-                copy_level(0, off_at(2));  // V_0 and V_1
-                if (ptp_grid_sync(a.ctrl->bar, 1, 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)ncta) < 0) {
-                    status = PTP_ERR_TIMEOUT;
-                    k = 0;
-                }
-            }
         }
     }
     Band bd;  // iteration 1: i_0 = 0, j_1 = min(1, rho - 1)
@@ -657,15 +730,10 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                     recompute(u, ent.x < 0, __int_as_float(ent.y), meta, r0, r1, l0, l1, g);
                 }
                 // the queue is refilled by the next round; after the last one
-                // only in the next iteration, behind the grid barrier, so warps
-                // done with pass 2 go on (to the level copy) at once
+                // only in the next iteration, behind the grid barrier
                 if (m0 + ROUND_CHUNKS < cta_m) __syncthreads();
             }
         }
-        // V_{k+1} into topleset order for the next iteration, by the warps
-        // counted from the last one down: in a narrow band not the band's
-        // warps, in a wide one the warps with the fewest queued vertices
-        if constexpr (FUSED && !PERM) copy_level(off_at((int)k + 1), off_at((int)k + 2));
         tot_active += n_active;
         tot_changed += n_changed;
 
@@ -712,7 +780,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
 
         const int any = __syncthreads_or(notconv);
         const int anyg = multi ? __syncthreads_or(gnotconv) : 0;
-        const long long failed = ptp_grid_sync(a.ctrl->bar, k + EP0, (any ? 1u : 0u) | (anyg ? 0x10000u : 0u),
+        const long long failed = ptp_grid_sync(a.ctrl->bar, k, (any ? 1u : 0u) | (anyg ? 0x10000u : 0u),
                                                &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)ncta,
                                                PTP_WAIT_CYCLES, true);
         if (failed < 0) {
@@ -960,7 +1028,10 @@ const void *fused_kernel(bool perm, bool labels, bool multi) {
     return labels ? (const void *)ptp_window<true, true, true> : (const void *)ptp_window<true, false, true>;
 }
 
-// Launch shape of a fused run: CTAs in all and how many run the BFS.  A
+// Launch shape of a fused run: CTAs in all, how many run the BFS and how
+// many copy the toplesets into place (topleset order only: as many as run
+// the BFS, whose levels they copy, one position per thread when a level
+// fits the producers' threads).  A
 // level's frontier grows like sqrt(n) on these meshes from one source (a few
 // thousand vertices at a million), and like n / rho from many: 2 sqrt(n m)
 // producer threads for m sources, from 2048 up to 8192 for one source and
@@ -971,7 +1042,7 @@ const void *fused_kernel(bool perm, bool labels, bool multi) {
 // bands are throughput-bound; a multi-source map (K close to rho, wide
 // frontiers from the first level) is paced by the BFS throughout.
 ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int m, bool perm, bool labels, int *block,
-                       int *grid, int *producers) {
+                       int *grid, int *producers, int *copiers) {
     *block = window_block(params->block);
     if (*block < 0) return PTP_ERR_ARG;
     int per_sm = 0;
@@ -986,14 +1057,15 @@ ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int m, bo
     int p = ((int)th + *block - 1) / *block;
     if (p > *grid / 4) p = *grid / 4;
     *producers = p > 0 ? p : 0;
+    *copiers = perm ? 0 : *producers;
     return PTP_OK;
 }
 
 }  // namespace
 
 int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params, int m, bool perm, bool labels) {
-    int block, grid, producers;
-    if (fused_shape(mesh, params, m, perm, labels, &block, &grid, &producers) != PTP_OK) return 0;
+    int block, grid, producers, copiers;
+    if (fused_shape(mesh, params, m, perm, labels, &block, &grid, &producers, &copiers) != PTP_OK) return 0;
     return producers;
 }
 
@@ -1011,8 +1083,8 @@ ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp
                               cudaStream_t s) {
     const int n = b->n;
     const int dev = mesh->device;
-    int block, grid, producers;
-    PTP_CHECK(fused_shape(mesh, params, m_max, perm, labels, &block, &grid, &producers));
+    int block, grid, producers, copiers;
+    PTP_CHECK(fused_shape(mesh, params, m_max, perm, labels, &block, &grid, &producers, &copiers));
     if (producers < 1) return PTP_ERR_TOO_LARGE;  // callers check ptp_internal_fused_producers first
     PTP_CHECK(ptp_internal_bfs_seed(mesh, b, src, m_dev, m_max, s));
     PTP_TRY(cudaMemsetAsync(b->ctrl, 0, sizeof(ptp_ctrl), s));
@@ -1083,6 +1155,7 @@ ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp
         a.feat_scale2 = 1073741824.0 / (diam * diam);
     }
     a.producers = producers;
+    a.copiers = copiers;
     a.level = b->level;
     a.queue_w = b->queue;
     a.off_w = b->off;

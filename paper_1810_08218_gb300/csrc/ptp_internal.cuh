@@ -57,6 +57,9 @@ struct ptp_ctrl {
     int ready;                   // levels published: off[0 .. ready] and the queue entries,
                                  // records and iperm of V_0 .. V_{ready-1} are final
                                  // (PTP_LEVELS_DONE once the BFS has ended)
+    unsigned long long cbar[2];  // barrier words of the copy CTAs (topleset order)
+    int copied;                  // toplesets in place: V_0 .. V_{copied-1} copied into
+                                 // topleset order (PTP_LEVELS_DONE once all are)
 };
 
 #define PTP_LEVELS_DONE 0x7fffffff

@@ -44,9 +44,9 @@ static_assert(FEAT_RING * FEAT_WORDS == PTP_FEAT_RING_WORDS, "feature ring size"
 // join the tested group of the learned multi-advance band: its predicted
 // delay after entry, but not before its schedule is visible to every CTA of
 // a fused launch.  There the toplesets of a batch b (r / SCHED_BATCH = b)
-// have their features summed at iteration 32 b + 31 (the last one copied at
-// 32 b + 30), their schedule inferred at 32 b + 32, and it is read one
-// iteration ahead, so it serves from iteration 32 b + 34 on.
+// have their features summed at iteration 32 b + 31 (the first at which the
+// last of them is in place), their schedule inferred at 32 b + 32, and it is
+// read one iteration ahead, so it serves from iteration 32 b + 34 on.
 __host__ __device__ __forceinline__ long long sched_due(int r, int sched) {
     const long long vis = (long long)SCHED_BATCH * (r / SCHED_BATCH) + SCHED_BATCH + 2;
     const long long pred = (long long)r + (sched > 1 ? sched : 1);

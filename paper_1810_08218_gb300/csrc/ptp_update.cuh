@@ -43,8 +43,11 @@ struct DistArgs {
     int *lab1;
     int band_mode;    // 0: Eq. lower_band; 1: fixed band, i_k = ceil(k / 2)
     const int *sched; // learned schedule per topleset, or NULL
-    // BFS inside the launch (fused window): the last `producers` CTAs
+    // BFS inside the launch (fused window): the last `producers` CTAs, and
+    // in topleset order the `copiers` CTAs before them, which put each
+    // topleset into place once the BFS has published it
     int producers;
+    int copiers;
     int *level;       // [n] BFS level, -1 unvisited
     int *queue_w;     // the BFS queue (= perm), written by the producers
     int *off_w;       // topleset offsets, written by the producers
