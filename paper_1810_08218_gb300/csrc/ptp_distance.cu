@@ -558,14 +558,24 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         const int start = bd.copy_lo < first ? bd.copy_lo : first;
         const bool testing = multi || k >= check_from;
         // multi: what the next group end needs (schedule and offsets from gend
-        // on), one value per thread 0..8, loaded now and put in shared memory
-        // at the end of the iteration
+        // on), one value per thread 0..8, copied into shared memory with
+        // cp.async now and waited for just before the CTA barrier at the end
+        // of the iteration (no register holds it across the band's work)
         int *const pf = s_pf[k & 1];
-        int pfv = 0x3fffffff;
         if constexpr (multi) {
             const int q = threadIdx.x, ge = s_mg[0];
-            if (q < 4) pfv = ge + q < slim ? __ldcg(a.sched + ge + q) : 0x3fffffff;
-            else if (q < 9) pfv = off_at(ge + q - 4 < a.n + 1 ? ge + q - 4 : a.n + 1);
+            const int *src = nullptr;
+            if (q < 4) {
+                if (ge + q < slim) src = a.sched + ge + q;
+                else pf[q] = 0x3fffffff;
+            } else if (q < 9) {
+                const int r = ge + q - 4 < a.n + 1 ? ge + q - 4 : a.n + 1;
+                src = a.off + (r < rho ? r : rho);
+            }
+            if (src) {
+                const unsigned dst = (unsigned)__cvta_generic_to_shared(pf + q);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" : : "r"(dst), "l"(src) : "memory");
+            }
         }
 
         int notconv = 0, gnotconv = 0, n_active = 0, n_changed = 0;
@@ -775,7 +785,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         // barrier, whose last step is a CTA barrier (two buffers by iteration
         // parity, so the next write waits a barrier)
         if constexpr (multi) {
-            if (threadIdx.x < 9) pf[threadIdx.x] = pfv;
+            if (threadIdx.x < 9) asm volatile("cp.async.wait_all;" : : : "memory");
         }
 
         const int any = __syncthreads_or(notconv);

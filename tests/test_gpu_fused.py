@@ -109,6 +109,27 @@ def test_fused_launch_shapes_and_modes(capi, pk):
     assert_same(a, b)
 
 
+def test_fused_repeated_runs_bit_identical(capi):
+    """The copy CTAs must copy every topleset position exactly once, in the
+    same ranges in every copy CTA, and publish a topleset only after all of
+    them have copied it; the window must not read a topleset before that.
+    A range that differed between copy CTAs (a position remapped twice, or
+    never) changed most distances of a map this size, and did so on some
+    runs only, so the fused map is repeated and compared with the two-step
+    map bit for bit each time."""
+    V, F = meshes.torus(768, 512, 1.0, 0.4, noise=0.01, seed=3)
+    S = [meshes.random_source(V.shape[0], 11)]
+    ref, first = both(capi, V, F, S)
+    assert_same(ref, first)
+    Vt = torch.from_numpy(f32(V)).cuda()
+    Ft = torch.from_numpy(np.ascontiguousarray(F, dtype=np.int32)).cuda()
+    mesh = capi.ptp_mesh_create(Vt, Ft)
+    for _ in range(4):
+        d = torch.full((V.shape[0],), -1.0, dtype=torch.float32, device="cuda")
+        st = capi.ptp_distance_from_sources(mesh, np.asarray(S, dtype=np.int32), capi.ptp_params_default(), d)
+        assert_same(ref, (d.cpu().numpy(), st, None))
+
+
 def test_fused_torus_1m_against_oracle(capi):
     V, F, S = meshes.torus_1m()
     a, b = both(capi, V, F, S)
