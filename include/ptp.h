@@ -101,14 +101,13 @@ typedef struct ptp_params {
                           band_mode 2: for each topleset r, the iterations after
                           it enters the band (at iteration r) until it is
                           expected to have converged; r joins the tested group
-                          from iteration max(r + schedule[r], 32 floor(r / 32)
-                          + 34) on (the second term is when a fused launch,
-                          which infers 32 toplesets at a time, can know it)   */
+                          from iteration r + max(schedule[r], 1) on            */
     const void *mlp_half;   /* band_mode 2 in ptp_distance_from_sources: DEVICE
                           array of PTP_MLP_NPARAM FP16 weights of the schedule
                           MLP.  The launch computes each topleset's window
-                          features once it is in topleset order and infers
-                          its schedule inside the launch, with the same
+                          features while it copies it into topleset order and
+                          infers its schedule before the iteration reaches
+                          it, with the same
                           arithmetic as ptp_window_features + ptp_mlp_infer, so
                           the two paths run the same iteration                  */
     float mlp_margin;       /* margin of that inference (see ptp_mlp_infer)       */

@@ -171,8 +171,11 @@ __device__ __noinline__ void bfs_producer(const DistArgs &a, int *stage_smem) {
 // Band position p of a topleset-ordered fused launch into place: the
 // producers' record there (meta, raw slots as original ids) gets its slots
 // remapped through iperm and the vertex's geometry copied from the original
-// mesh.  Every slot's vertex must have its position (iperm) by then.
-__device__ __forceinline__ void copy_position(const DistArgs &a, int p) {
+// mesh.  Every slot's vertex must have its position (iperm) by then.  With
+// ft, also the vertex's window-feature terms (ptp_schedule.cuh) from the
+// values just copied: the same inputs ptp_window_features reads from a
+// toplesets handle, so the sums come out the same.
+__device__ __forceinline__ void copy_position(const DistArgs &a, int p, FeatTerms *ft, float3 xs) {
     const int n = a.n;
     const int v = __ldcg(a.perm + p);
     const int4 s0 = __ldcg(a.ring_w + p), s1 = __ldcg(a.ring_w + n + p);
@@ -188,6 +191,37 @@ __device__ __forceinline__ void copy_position(const DistArgs &a, int p) {
     for (int q = 0; q < PTP_TRI; ++q) a.tgeom_w[(size_t)q * n + p] = g[q];
     a.elen_w[p] = e0;
     a.elen_w[n + p] = e1;
+    if (ft) {
+        const float el[PTP_RING] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+        float gb[PTP_TRI];
+#pragma unroll
+        for (int q = 0; q < PTP_TRI; ++q) gb[q] = g[q].x;
+        *ft = feat_terms(__ldcg(a.meta + p), el, gb, make_float3(x.x, x.y, x.z), xs, a.feat_scale, a.feat_scale2);
+    }
+}
+
+// Learned multi-advance band in a fused launch: the schedule of topleset r
+// (one warp, in a copy CTA), from the feature sums its copy accumulated
+// (ptp_schedule.cuh) and the MLP whose FP16 weights are in `w`; the sums'
+// ring slot is cleared for reuse.  Toplesets at or past `lim` are skipped,
+// and V_0 (the sources) needs no schedule.
+__device__ __noinline__ void infer_one(const DistArgs &a, const __half *w, int r, int lim) {
+    if (r >= lim) return;
+    const int lane = threadIdx.x & 31;
+    unsigned long long *acc = a.facc + (size_t)(r % FEAT_RING) * FEAT_WORDS;
+    if (r >= 1) {
+        const int om = __ldcg(a.off + r - 1), o0 = __ldcg(a.off + r), o1 = __ldcg(a.off + r + 1);
+        unsigned long long v[FEAT_WORDS];
+#pragma unroll
+        for (int q = 0; q < FEAT_WORDS; ++q) v[q] = __ldcg(acc + q);
+        float x[MLP_NIN];
+        feat_finalize(v, o1 - o0, o0 - om, r, a.n, x);
+        const float y = mlp_forward_warp(w, x);
+        if (lane == 0) a.sched_w[r] = sched_from_y(y, a.mlp_margin, 1 << 20);
+    }
+    __syncwarp();
+    // the slot serves topleset r + FEAT_RING next (V_0's sums are never used)
+    if (lane < FEAT_WORDS) acc[lane] = 0ull;
 }
 
 // Copy CTAs of a topleset-ordered fused launch: the a.copiers CTAs before
@@ -212,6 +246,14 @@ __device__ __forceinline__ void copy_position(const DistArgs &a, int p) {
 // ctrl->copied before they read the copied toplesets and the offsets;
 // ctrl->copied >= r + 1 implies ctrl->ready >= r + 2, so off[0 .. r+2] are
 // published as well.  Copy CTAs never wait for the window CTAs.
+//
+// LEARN (the learned multi-advance band): the copy also sums each
+// topleset's window features (one topleset at a time, so that a warp adds
+// to one feature slot), a round takes at most FEAT_RING toplesets (their
+// slots), and after the barrier one warp per topleset infers its schedule
+// (infer_one); a second barrier precedes the publication, so ctrl->copied
+// >= r + 1 also means that schedule[r] is written.
+template <bool LEARN>
 __device__ __noinline__ void level_copier(const DistArgs &a) {
     const int C = a.copiers;
     const int cid = (int)blockIdx.x - ((int)gridDim.x - a.producers - C);
@@ -219,10 +261,28 @@ __device__ __noinline__ void level_copier(const DistArgs &a) {
     const int cwarp = (int)(threadIdx.x >> 5) * C + cid;  // warps interleaved across the copy CTAs
     const int ncw = (int)(blockDim.x >> 5) * C;
     constexpr int TO_RHO = 0x7fffffff;  // the round ends at rho (the BFS has ended)
+    constexpr unsigned BFS_ENDED = 1u << 30;
     __shared__ int s_now[2];
+    __shared__ __half s_w[LEARN ? MLP_NPARAM_ : 1];      // MLP weights
+    __shared__ int s_off[LEARN ? FEAT_RING + 1 : 1];     // the round's offsets
+    __shared__ float s_xs[3];                            // the first source's position
+    float3 xs = make_float3(0.0f, 0.0f, 0.0f);
+    if constexpr (LEARN) {
+        const __half *wg = (const __half *)a.mlp_w;
+        for (int q = threadIdx.x; q < MLP_NPARAM_; q += blockDim.x) s_w[q] = wg[q];
+        if (threadIdx.x == 0) {
+            const float4 x0 = __ldg(a.opos + __ldcg(a.perm));
+            s_xs[0] = x0.x;
+            s_xs[1] = x0.y;
+            s_xs[2] = x0.z;
+        }
+        __syncthreads();
+        xs = make_float3(s_xs[0], s_xs[1], s_xs[2]);
+    }
     unsigned long long prev_hi[2] = {0ull, 0ull};
+    long long e = 1;         // the copy CTAs' barrier epoch
     int done = 0, upto = 1;  // the first round copies V_0
-    for (long long e = 1;; ++e) {
+    while (true) {
         if (threadIdx.x == 0) {
             int now = 0, ok = 1;
             const long long t0 = clock64();
@@ -245,99 +305,60 @@ __device__ __noinline__ void level_copier(const DistArgs &a) {
         }
         __syncthreads();
         if (!s_now[0]) return;
-        if (upto == TO_RHO) upto = s_now[1];  // every copy CTA has seen the BFS end
-        const int pb = __ldcg(a.off + done), pe = __ldcg(a.off + upto);
-        const int cb = pb & ~31;
-        const int rch = pe > cb ? (pe - cb + 31) >> 5 : 0;
-        for (int c = cwarp; c < rch; c += ncw) {
-            const int p = cb + c * 32 + lane;
-            if (p >= pb && p < pe) copy_position(a, p);
+        const int rho_seen = s_now[1];  // s_now is rewritten in the next round
+        if (upto == TO_RHO) upto = rho_seen;  // every copy CTA has seen the BFS end
+        if (LEARN && upto - done > FEAT_RING) upto = done + FEAT_RING;
+        if constexpr (LEARN) {
+            if (threadIdx.x <= upto - done) s_off[threadIdx.x] = __ldcg(a.off + done + (int)threadIdx.x);
+            __syncthreads();
+            int cbase = 0;  // chunks of the round's earlier toplesets
+            for (int r = done; r < upto; ++r) {
+                const int pb = s_off[r - done], pe = s_off[r - done + 1];
+                const int cb = pb & ~31;
+                const int rch = pe > cb ? (pe - cb + 31) >> 5 : 0;
+                unsigned long long *acc = a.facc + (size_t)(r % FEAT_RING) * FEAT_WORDS;
+                int c0 = (cwarp - cbase) % ncw;
+                if (c0 < 0) c0 += ncw;
+                for (int c = c0; c < rch; c += ncw) {  // warp-uniform
+                    const int p = cb + c * 32 + lane;
+                    const bool have = p >= pb && p < pe;
+                    FeatTerms ft = {};
+                    if (have) copy_position(a, p, &ft, xs);
+                    feat_warp_add(acc, ft, have);
+                }
+                cbase += rch;
+            }
+        } else {
+            const int pb = __ldcg(a.off + done), pe = __ldcg(a.off + upto);
+            const int cb = pb & ~31;
+            const int rch = pe > cb ? (pe - cb + 31) >> 5 : 0;
+            for (int c = cwarp; c < rch; c += ncw) {
+                const int p = cb + c * 32 + lane;
+                if (p >= pb && p < pe) copy_position(a, p, nullptr, xs);
+            }
         }
         // the BFS's progress for the next range, from copy CTA 0 only: how
         // many toplesets past upto are copyable, or BFS_ENDED (the barrier
         // sums the values of all its epochs in 32 bits, so they stay small)
-        constexpr unsigned BFS_ENDED = 1u << 30;
         unsigned seen = 0;
         if (cid == 0 && threadIdx.x == 0) {
             const int rd = ptp_ld_acquire_s32(&a.ctrl->ready);  // >= upto + 1, seen above
             seen = rd == PTP_LEVELS_DONE ? BFS_ENDED : (unsigned)min(rd - (upto + 1), 1 << 20);
         }
-        // s_now is rewritten only after this barrier's last CTA barrier
-        const long long sum = ptp_grid_sync(a.ctrl->cbar, e, seen, &a.ctrl->abort, &a.ctrl->status, prev_hi,
+        const long long sum = ptp_grid_sync(a.ctrl->cbar, e++, seen, &a.ctrl->abort, &a.ctrl->status, prev_hi,
                                             (unsigned)C);
         if (sum < 0) return;
-        const bool last = upto == s_now[1];  // V_{rho-1} is in place
+        if constexpr (LEARN) {
+            // every feature sum of the round is complete: the schedules
+            for (int r = done + cwarp; r < upto; r += ncw) infer_one(a, s_w, r, upto);  // warp-uniform
+            if (ptp_grid_sync(a.ctrl->cbar, e++, 0u, &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)C) < 0)
+                return;
+        }
+        const bool last = upto == rho_seen;  // V_{rho-1} is in place
         if (cid == 0 && threadIdx.x == 0) ptp_st_release_s32(&a.ctrl->copied, last ? PTP_LEVELS_DONE : upto);
         if (last) return;
         done = upto;
         upto = sum >= BFS_ENDED ? TO_RHO : done + (sum > 0 ? (int)sum : 1);
-    }
-}
-
-// Learned multi-advance band in a fused launch: the schedule of topleset r
-// (one warp), from the feature sums its copy accumulated (ptp_schedule.cuh)
-// and the MLP whose FP16 weights are in `w`; the sums' ring slot is cleared
-// for reuse.  Toplesets at or past `lim` (rho once known) are empty and
-// skipped, and V_0 (the sources) needs no schedule.
-__device__ __noinline__ void infer_one(const DistArgs &a, const __half *w, int r, int lim) {
-    if (r >= lim) return;
-    const int lane = threadIdx.x & 31;
-    unsigned long long *acc = a.facc + (size_t)(r % FEAT_RING) * FEAT_WORDS;
-    if (r >= 1) {
-        const int om = __ldcg(a.off + r - 1), o0 = __ldcg(a.off + r), o1 = __ldcg(a.off + r + 1);
-        unsigned long long v[FEAT_WORDS];
-#pragma unroll
-        for (int q = 0; q < FEAT_WORDS; ++q) v[q] = __ldcg(acc + q);
-        float x[MLP_NIN];
-        feat_finalize(v, o1 - o0, o0 - om, r, a.n, x);
-        const float y = mlp_forward_warp(w, x);
-        if (lane == 0) a.sched_w[r] = sched_from_y(y, a.mlp_margin, 1 << 20);
-    }
-    __syncwarp();
-    // the slot serves topleset r + FEAT_RING next (V_0's sums are never used)
-    if (lane < FEAT_WORDS) acc[lane] = 0ull;
-}
-
-// Learned multi-advance band in a fused launch: the window-feature sums of
-// toplesets r0 .. r0 + 31 (already in topleset order;
-// boff[t] = off[r0 + t]) into their slots of the feature ring, by every warp
-// of the window CTAs at once.  Kept out of line: it runs once every
-// SCHED_BATCH iterations and must not add to the iteration's registers.
-__device__ __noinline__ void feature_pass(const DistArgs &a, int r0, int gwarp, int nwarps, const int *boff,
-                                          const float *xs3) {
-    const int lane = threadIdx.x & 31;
-    const int pb = boff[0], pe = boff[SCHED_BATCH];
-    const int cb = pb & ~31;
-    const int rch = pe > cb ? (pe - cb + 31) >> 5 : 0;
-    const float3 xs = make_float3(xs3[0], xs3[1], xs3[2]);
-    for (int c = gwarp; c < rch; c += nwarps) {  // warp-uniform
-        const int p = cb + c * 32 + lane;
-        const bool have = p >= pb && p < pe;
-        int r = -1;
-        FeatTerms ft = {};
-        if (have) {
-            int lo = 0, hi = SCHED_BATCH;  // largest t with boff[t] <= p
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (boff[mid] <= p) lo = mid;
-                else hi = mid;
-            }
-            r = r0 + lo;
-            const float4 l0 = __ldcg(a.elen + p), l1 = __ldcg(a.elen + a.n + p), x = __ldcg(a.pos + p);
-            const float el[PTP_RING] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
-            float gb[PTP_TRI];
-#pragma unroll
-            for (int t = 0; t < PTP_TRI; ++t) gb[t] = __ldcg(a.tgeom + (size_t)t * a.n + p).x;
-            ft = feat_terms(__ldcg(a.meta + p), el, gb, make_float3(x.x, x.y, x.z), xs, a.feat_scale, a.feat_scale2);
-        }
-        bool todo = have;
-        while (__any_sync(0xffffffffu, todo)) {  // warp-uniform: one add per topleset present
-            const int lead = __ffs(__ballot_sync(0xffffffffu, todo)) - 1;
-            const int rl = __shfl_sync(0xffffffffu, r, lead);
-            const bool mine = todo && r == rl;
-            feat_warp_add(a.facc + (size_t)(rl % FEAT_RING) * FEAT_WORDS, ft, mine);
-            todo = todo && !mine;
-        }
     }
 }
 
@@ -393,7 +414,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         }
         if constexpr (!PERM) {
             if ((int)blockIdx.x >= (int)gridDim.x - a.producers - a.copiers) {
-                level_copier(a);
+                level_copier<MULTI>(a);
                 return;
             }
         }
@@ -476,22 +497,6 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     // what iteration k needs: V_0 .. V_k in place (topleset order), or the
     // offsets off[0 .. k+3] (original order)
     auto need_for = [](long long kk) { return (int)kk + (PERM ? 3 : 1); };
-    __shared__ float s_xs[3];  // the first source's position
-    __shared__ int s_boff[SCHED_BATCH + 1];
-    __shared__ __half s_mlp[(FUSED && MULTI) ? MLP_NPARAM_ : 1];
-    if constexpr (FUSED && MULTI) {
-        {
-            const __half *wg = (const __half *)a.mlp_w;
-            for (int q = threadIdx.x; q < MLP_NPARAM_; q += blockDim.x) s_mlp[q] = wg[q];
-            if (threadIdx.x == 0) {
-                const float4 xs = __ldg(a.opos + __ldcg(a.perm));
-                s_xs[0] = xs.x;
-                s_xs[1] = xs.y;
-                s_xs[2] = xs.z;
-            }
-            __syncthreads();
-        }
-    }
     if constexpr (FUSED) {
         if (!wait_levels(need_for(1))) {
             status = PTP_ERR_TIMEOUT;
@@ -532,20 +537,6 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             if (!wait_levels(need_for(k))) {
                 status = PTP_ERR_TIMEOUT;
                 break;
-            }
-            if constexpr (MULTI) {
-                // every SCHED_BATCH iterations: the feature sums of the last
-                // SCHED_BATCH toplesets copied, then (one iteration later, once
-                // the sums are complete) their schedule, one topleset per warp
-                if ((k % SCHED_BATCH) == SCHED_BATCH - 1) {
-                    const int r0 = (int)k - (SCHED_BATCH - 1);
-                    if (threadIdx.x <= SCHED_BATCH) s_boff[threadIdx.x] = off_at(r0 + (int)threadIdx.x);
-                    __syncthreads();
-                    feature_pass(a, r0, gwarp, nwarps, s_boff, s_xs);
-                }
-                if (k >= SCHED_BATCH && (k % SCHED_BATCH) == 0)
-                    for (int l = gwarp; l < SCHED_BATCH; l += nwarps)  // warp-uniform
-                        infer_one(a, s_mlp, (int)k - SCHED_BATCH + l, rho);
             }
         }
         const int j = k < rho ? (int)k : rho - 1;

@@ -1,6 +1,6 @@
-// Device side of the learned window schedule, shared by the window kernel
-// (features accumulated while the fused launch copies each topleset, the MLP
-// run inside the launch) and by ptp_window_features / ptp_mlp_infer (the same
+// Device side of the learned window schedule, shared by the fused launch's
+// copy CTAs (features summed while they copy each topleset into place, the
+// MLP run right after) and by ptp_window_features / ptp_mlp_infer (the same
 // features and the same forward pass for a toplesets handle), so that both
 // paths infer bit-identical schedules.
 //
@@ -33,24 +33,19 @@ constexpr int MLP_OW1 = 0, MLP_OB1 = MLP_OW1 + MLP_H * MLP_NIN, MLP_OW2 = MLP_OB
 constexpr int MLP_NPARAM_ = MLP_OB3 + 1;
 static_assert(MLP_NPARAM_ == PTP_MLP_NPARAM, "parameter count");
 
-// Toplesets whose schedule the fused launch infers together (one per lane),
-// and the ring of per-topleset feature accumulators it keeps.
-constexpr int SCHED_BATCH = 32;
+// The ring of per-topleset feature accumulators a fused launch keeps (a copy
+// round takes at most this many toplesets).
 constexpr int FEAT_RING = 64;
 constexpr int FEAT_WORDS = 8;  // per topleset: se, se2, sr, sr2, edges, count, amin bits, pad
 static_assert(FEAT_RING * FEAT_WORDS == PTP_FEAT_RING_WORDS, "feature ring size");
 
 // Iteration from which topleset r, entering the band at iteration r, may
 // join the tested group of the learned multi-advance band: its predicted
-// delay after entry, but not before its schedule is visible to every CTA of
-// a fused launch.  There the toplesets of a batch b (r / SCHED_BATCH = b)
-// have their features summed at iteration 32 b + 31 (the first at which the
-// last of them is in place), their schedule inferred at 32 b + 32, and it is
-// read one iteration ahead, so it serves from iteration 32 b + 34 on.
+// delay after entry (at least one iteration).  In a fused launch the
+// schedule of V_r is written before V_r is published to the window, so it
+// is known by then.
 __host__ __device__ __forceinline__ long long sched_due(int r, int sched) {
-    const long long vis = (long long)SCHED_BATCH * (r / SCHED_BATCH) + SCHED_BATCH + 2;
-    const long long pred = (long long)r + (sched > 1 ? sched : 1);
-    return pred > vis ? pred : vis;
+    return (long long)r + (sched > 1 ? sched : 1);
 }
 
 __device__ __forceinline__ long long fixq(double v, double scale) { return llrint(v * scale); }
