@@ -72,7 +72,7 @@ def assert_same(a, b, trace=False):
             assert np.array_equal(t0[f], t1[f]), f
 
 
-@pytest.mark.parametrize("name", ["flat65", "sphere_l5", "random", "multi", "two_components", "triangle"])
+@pytest.mark.parametrize("name", ["flat65", "sphere_l5", "random", "multi", "two_components", "triangle", "strip"])
 def test_fused_equals_two_step(capi, name):
     if name == "flat65":
         V, F, S = meshes.flat65()
@@ -85,6 +85,10 @@ def test_fused_equals_two_step(capi, name):
     elif name == "multi":
         V, F = meshes.icosphere(4)
         S = [5, 900, 5, 2000, 17]
+    elif name == "strip":
+        # 2000 small toplesets: the copy CTAs trail the BFS and copy many per round
+        V, F = meshes.grid(2000, 4, jitter=0.1, seed=7)
+        S = [0]
     elif name == "two_components":
         V1, F1 = meshes.grid(12, 12, jitter=0.1, seed=4)
         V = np.concatenate([V1, V1 + [2.0, 0.0, 0.0]])

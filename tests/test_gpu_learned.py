@@ -157,21 +157,34 @@ def test_learned_band_is_safe_with_any_schedule(capi, kind):
         assert sl["iterations"] <= sp["iterations"]
 
 
-def test_fused_learned_band_equals_the_two_step_learned_band(capi):
-    """The fused launch computes each topleset's features while it copies it
-    and infers the schedule inside the launch, with the same arithmetic as
-    ptp_window_features + ptp_mlp_infer: the same iteration, the same map."""
+@pytest.mark.parametrize("case", ["sphere", "sphere_grid7", "sphere_block128", "strip"])
+def test_fused_learned_band_equals_the_two_step_learned_band(capi, case):
+    """The fused launch's copy CTAs compute each topleset's features while
+    they copy it and infer its schedule before publishing it, with the same
+    arithmetic as ptp_window_features + ptp_mlp_infer: the same iteration,
+    the same map.  Also with one copy CTA (a 7-CTA grid), 4 warps per CTA,
+    and on a 2000 x 4 strip, whose thousands of small toplesets make the copy
+    CTAs fall behind the BFS and take the largest rounds (the feature ring's
+    64 toplesets)."""
     from paper_1810_08218_gb300 import learned
 
     w, meta = learned.load_weights()
-    V, F, S = meshes.sphere_l7(seed=11)
+    if case == "strip":
+        V, F = meshes.grid(2000, 4, jitter=0.1, seed=7)
+        S = np.array([0], np.int32)
+    else:
+        V, F, S = meshes.sphere_l7(seed=11)
     n = V.shape[0]
+    shape = {"sphere_grid7": {"grid": 7}, "sphere_block128": {"block": 128}}.get(case, {})
     mesh, tops = mesh_tops(capi, V, F, S)
     sched = learned.schedule(tops, w, meta["margin"])
-    d2, s2 = run(capi, tops, n, eps=FIX, band_mode=2, schedule=sched)
+    d2, s2 = run(capi, tops, n, eps=FIX, band_mode=2, schedule=sched, **shape)
     wh = learned.half_weights(w)
     d = torch.empty(n, dtype=torch.float32, device="cuda")
-    sf = capi.ptp_distance_from_sources(mesh, S, learned.learned_params(wh, meta["margin"]), d)
+    pf = learned.learned_params(wh, meta["margin"])
+    for k, v in shape.items():
+        setattr(pf, k, v)
+    sf = capi.ptp_distance_from_sources(mesh, S, pf, d)
     assert sf["status"] == 0 and sf["iterations"] == s2["iterations"] and sf["band_updates"] == s2["band_updates"]
     assert np.array_equal(d.cpu().numpy(), d2)
 
