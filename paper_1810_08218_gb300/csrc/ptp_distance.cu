@@ -522,10 +522,16 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
     // iteration no registers; the next write comes only after a CTA barrier
     // that every reader of the previous values has passed.
     __shared__ int s_mg[2];
+    // The group's test result of iteration k: set to 1 by any thread whose
+    // group vertex failed, read and cleared by thread 0 after the CTA
+    // barrier that ends the iteration's work; two slots by parity, so a slot
+    // is written again only two barriers after thread 0 cleared it.
+    __shared__ int s_gfail[2];
     if constexpr (MULTI) {
         if (threadIdx.x == 0) {
             s_mg[0] = 1;
             s_mg[1] = 0;
+            s_gfail[0] = s_gfail[1] = 0;
         }
         __syncthreads();
     }
@@ -569,7 +575,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
             }
         }
 
-        int notconv = 0, gnotconv = 0, n_active = 0, n_changed = 0;
+        int notconv = 0, n_active = 0, n_changed = 0;
         float maxrel = 0.0f;
         double errsum = 0.0;
         const int base = start & ~31;
@@ -608,7 +614,7 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
                     // difference of two floats is exact in double)
                     const double o = dold, delta = o - (double)dnew;
                     const bool fail = !(isfinite(o) && delta < __dadd_rn(__dmul_rn(a.eps, o), a.eps_abs));
-                    if (fail && in_g) gnotconv = 1;
+                    if (fail && in_g) s_gfail[k & 1] = 1;
                     if (fail && a.conv_trace) atomicMax(a.conv_trace + topleset_of(a.off, rho, u), (int)k);
                     if (in_vi && testing) {
                     if (fail) notconv = 1;
@@ -780,7 +786,13 @@ __global__ void __launch_bounds__(DIST_THREADS, PTP_DIST_MIN_BLOCKS) ptp_window(
         }
 
         const int any = __syncthreads_or(notconv);
-        const int anyg = multi ? __syncthreads_or(gnotconv) : 0;
+        int anyg = 0;
+        if constexpr (multi) {
+            if (threadIdx.x == 0) {  // only thread 0's value enters the grid barrier
+                anyg = s_gfail[k & 1];
+                s_gfail[k & 1] = 0;
+            }
+        }
         const long long failed = ptp_grid_sync(a.ctrl->bar, k, (any ? 1u : 0u) | (anyg ? 0x10000u : 0u),
                                                &a.ctrl->abort, &a.ctrl->status, prev_hi, (unsigned)ncta,
                                                PTP_WAIT_CYCLES, true);
