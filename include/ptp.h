@@ -106,10 +106,10 @@ typedef struct ptp_params {
                           array of PTP_MLP_NPARAM FP16 weights of the schedule
                           MLP.  The launch computes each topleset's window
                           features while it copies it into topleset order and
-                          infers its schedule before the iteration reaches
-                          it, with the same
-                          arithmetic as ptp_window_features + ptp_mlp_infer, so
-                          the two paths run the same iteration                  */
+                          infers its schedule before the iteration reaches it,
+                          with the same arithmetic as ptp_window_features +
+                          ptp_mlp_infer, so the two paths run the same
+                          iteration                                             */
     float mlp_margin;       /* margin of that inference (see ptp_mlp_infer)       */
     int32_t reserved2;      /* must be 0                                           */
     int32_t *conv_trace;    /* optional DEVICE array [rho] (ptp_distance only),
