@@ -1077,7 +1077,7 @@ ptp_status fused_shape(const ptp_mesh *mesh, const ptp_params *params, int m, bo
 }  // namespace
 
 int ptp_internal_fused_producers(const ptp_mesh *mesh, const ptp_params *params, int m, bool perm, bool labels) {
-    int block, grid, producers, copiers;
+    int block = 0, grid = 0, producers = 0, copiers = 0;
     if (fused_shape(mesh, params, m, perm, labels, &block, &grid, &producers, &copiers) != PTP_OK) return 0;
     return producers;
 }
@@ -1096,7 +1096,7 @@ ptp_status ptp_internal_fused(const ptp_mesh *mesh, ptp_multi_bufs *b, const ptp
                               cudaStream_t s) {
     const int n = b->n;
     const int dev = mesh->device;
-    int block, grid, producers, copiers;
+    int block = 0, grid = 0, producers = 0, copiers = 0;
     PTP_CHECK(fused_shape(mesh, params, m_max, perm, labels, &block, &grid, &producers, &copiers));
     if (producers < 1) return PTP_ERR_TOO_LARGE;  // callers check ptp_internal_fused_producers first
     PTP_CHECK(ptp_internal_bfs_seed(mesh, b, src, m_dev, m_max, s));
