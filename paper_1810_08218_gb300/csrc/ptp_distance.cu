@@ -309,7 +309,7 @@ __device__ __noinline__ void level_copier(const DistArgs &a) {
         if (upto == TO_RHO) upto = rho_seen;  // every copy CTA has seen the BFS end
         if (LEARN && upto - done > FEAT_RING) upto = done + FEAT_RING;
         if constexpr (LEARN) {
-            if (threadIdx.x <= upto - done) s_off[threadIdx.x] = __ldcg(a.off + done + (int)threadIdx.x);
+            for (int q = threadIdx.x; q <= upto - done; q += blockDim.x) s_off[q] = __ldcg(a.off + done + q);
             __syncthreads();
             int cbase = 0;  // chunks of the round's earlier toplesets
             for (int r = done; r < upto; ++r) {

@@ -157,7 +157,7 @@ def test_learned_band_is_safe_with_any_schedule(capi, kind):
         assert sl["iterations"] <= sp["iterations"]
 
 
-@pytest.mark.parametrize("case", ["sphere", "sphere_grid7", "sphere_block128", "strip"])
+@pytest.mark.parametrize("case", ["sphere", "sphere_grid7", "sphere_block128", "strip", "strip_block64"])
 def test_fused_learned_band_equals_the_two_step_learned_band(capi, case):
     """The fused launch's copy CTAs compute each topleset's features while
     they copy it and infer its schedule before publishing it, with the same
@@ -165,17 +165,17 @@ def test_fused_learned_band_equals_the_two_step_learned_band(capi, case):
     the same map.  Also with one copy CTA (a 7-CTA grid), 4 warps per CTA,
     and on a 2000 x 4 strip, whose thousands of small toplesets make the copy
     CTAs fall behind the BFS and take the largest rounds (the feature ring's
-    64 toplesets)."""
+    64 toplesets, whose 65 offsets a 64-thread CTA stages in two passes)."""
     from paper_1810_08218_gb300 import learned
 
     w, meta = learned.load_weights()
-    if case == "strip":
+    if case.startswith("strip"):
         V, F = meshes.grid(2000, 4, jitter=0.1, seed=7)
         S = np.array([0], np.int32)
     else:
         V, F, S = meshes.sphere_l7(seed=11)
     n = V.shape[0]
-    shape = {"sphere_grid7": {"grid": 7}, "sphere_block128": {"block": 128}}.get(case, {})
+    shape = {"sphere_grid7": {"grid": 7}, "sphere_block128": {"block": 128}, "strip_block64": {"block": 64}}.get(case, {})
     mesh, tops = mesh_tops(capi, V, F, S)
     sched = learned.schedule(tops, w, meta["margin"])
     d2, s2 = run(capi, tops, n, eps=FIX, band_mode=2, schedule=sched, **shape)
