@@ -47,3 +47,31 @@ def test_accuracy_reference_distances():
     e = accuracy._exact("sphere_l7", V, np.array([0]))
     assert np.allclose(e, [0.0, math.pi, math.pi / 2, math.pi / 2], atol=1e-12)
     assert accuracy._exact("torus_1m", V, np.array([0])) is None
+
+
+def test_recorded_traffic_is_dropped_when_the_kernel_code_changes(tmp_path, monkeypatch):
+    """The bench line's roofline.traffic comes from a committed ncu figure
+    keyed by a hash of the window kernel's sources without comments and
+    whitespace: kept across a comment edit, dropped (None) once the code
+    differs from the code the capture was taken on."""
+    import json
+    import shutil
+
+    import bench
+
+    csrc = tmp_path / "paper_1810_08218_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in ("ptp_distance.cu", "ptp_update.cuh", "ptp_internal.cuh", "ptp_schedule.cuh"):
+        shutil.copy(os.path.join(ROOT, "paper_1810_08218_gb300", "csrc", f), csrc / f)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    record = {"torus_1m": {"kernel_source_sha256": bench._kernel_source_hash(), "dram_bytes_per_launch": 123.0}}
+    (tmp_path / "profiles" / "ptp_window_traffic.json").write_text(json.dumps(record))
+    assert bench._traffic("torus_1m") == 123.0
+    assert bench._traffic("sphere_l7") is None  # no capture recorded for it
+    src = csrc / "ptp_distance.cu"
+    text = src.read_text()
+    src.write_text(text + "\n// a comment only\n/* and a block\n   comment */\n\n")
+    assert bench._traffic("torus_1m") == 123.0
+    src.write_text(text + "\nstatic int one_more_line_of_code = 1;\n")
+    assert bench._traffic("torus_1m") is None
