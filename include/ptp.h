@@ -239,10 +239,13 @@ ptp_status ptp_distance(ptp_toplesets_t *tops, const ptp_params *params, float *
  * Computes what ptp_toplesets followed by ptp_distance computes (Sec. 4.1,
  * Sec. 4.2; the same iterates, hence bit-identical distances), but the BFS
  * runs inside the window launch: a few CTAs expand the toplesets level by
- * level while the others iterate, each iteration k waiting (on the device)
- * only until V_0 .. V_{k+1} exist.  As in the paper's multi-source GPU runs
- * (Sec. 5.1) the vertices are not rearranged: the band is walked through the
- * BFS queue and every per-vertex array stays in the original order.
+ * level, a few more put each finished level into topleset order (Sec. 4.3:
+ * slots remapped to positions, geometry copied), and the others iterate,
+ * each iteration k waiting (on the device) only until V_0 .. V_k are in
+ * place.  The distances are gathered back to the original order at the end.
+ * (The multi-source calls, ptp_voronoi and ptp_fps, run the same launch
+ * without the rearrangement, as the paper's multi-source GPU runs do, Sec.
+ * 5.1: the band is walked through the BFS queue in the original order.)
  *  sources   [m] vertex indices (ptr_kind), m >= 1; repeats are ignored.
  *  d_out     [n_verts] float32 DEVICE, original order; +inf if unreachable.
  *  params    as ptp_distance; schedule must be NULL (PTP_ERR_ARG); the
