@@ -154,6 +154,13 @@ def test_fused_argument_errors(capi):
     p.schedule = sched.data_ptr()
     with pytest.raises(capi.PTPError):
         capi.ptp_distance_from_sources(mesh, S, p, d)
+    # an empty source list, and a mesh with no faces
+    with pytest.raises(capi.PTPError) as e:
+        capi.ptp_distance_from_sources(mesh, np.array([], dtype=np.int32), capi.ptp_params_default(), d)
+    assert e.value.status == capi.PTP_ERR_ARG
+    with pytest.raises(capi.PTPError) as e:
+        capi.ptp_mesh_create(torch.from_numpy(f32(V)).cuda(), torch.zeros((0, 3), dtype=torch.int32, device="cuda"))
+    assert e.value.status == capi.PTP_ERR_ARG
 
 
 def test_fused_device_sources_and_geodesic(capi):
